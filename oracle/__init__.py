@@ -1,0 +1,142 @@
+"""FP64 CPU oracle for the 3-D DFT -- test infrastructure only.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA library
+in ``paper_1506_07933_gb300``; the two meet only in the tests, on inputs drawn
+from the seeded generators of ``paper_1506_07933_gb300.synth`` (which hold none
+of the transform's arithmetic).
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, long-double unit roots);
+this module only marshals numpy arrays into it.  What each function computes
+and which passage of AccFFT it follows is stated in ``oracle.c``:
+
+* forward c2c, unscaled, axes N2, N1, N0 (Algorithm 1, left column);
+* backward c2c, axes N0, N1, N2 (Algorithm 1, right column), times 1/N
+  (Section 2, footnote 2);
+* r2c = c2c of the real field with k2 = 0 .. n2/2 kept; c2r its inverse on
+  Hermitian-consistent input (Section 1 feature list: R2C, C2C, C2R).
+
+``method="naive"`` is the O(n^2) definition per axis (long-double sums);
+``method="fft"`` is a recursive mixed-radix (2, 3, 5) Cooley-Tukey, the
+large-size oracle and the timed CPU baseline.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+METHODS = {"naive": 0, "fft": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so with gcc (OpenMP on)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i64, dp, c_int = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+        lib.orc_dft_axis.argtypes = [dp, i64, i64, i64, c_int, c_int, c_int]
+        lib.orc_c2c_3d.argtypes = [dp, dp, i64, i64, i64, c_int, c_int, c_int]
+        lib.orc_r2c_3d.argtypes = [dp, dp, i64, i64, i64, c_int, c_int]
+        lib.orc_c2r_3d.argtypes = [dp, dp, i64, i64, i64, c_int, c_int]
+        for f in (lib.orc_dft_axis, lib.orc_c2c_3d, lib.orc_r2c_3d, lib.orc_c2r_3d):
+            f.restype = c_int
+        lib.orc_max_threads.restype = c_int
+        _lib = lib
+    return _lib
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+def _threads(nthreads):
+    return max_threads() if nthreads is None else int(nthreads)
+
+
+def _check(status: int):
+    if status != 0:
+        raise RuntimeError("oracle error %d" % status)
+
+
+def _c128(x):
+    return np.ascontiguousarray(x, dtype=np.complex128)
+
+
+def c2c(x, direction: int = -1, method: str = "fft", nthreads=None) -> np.ndarray:
+    """3-D c2c of a complex [n0, n1, n2] array; direction -1 forward, +1 backward (x 1/N)."""
+    x = _c128(x)
+    if x.ndim != 3:
+        raise ValueError("expected a 3-D array")
+    out = np.empty_like(x)
+    n0, n1, n2 = x.shape
+    _check(_load().orc_c2c_3d(x.ctypes.data, out.ctypes.data, n0, n1, n2, int(direction),
+                              METHODS[method], _threads(nthreads)))
+    return out
+
+
+def r2c(x, method: str = "fft", nthreads=None) -> np.ndarray:
+    """3-D r2c of a real [n0, n1, n2] array -> complex [n0, n1, n2//2 + 1]."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.ndim != 3:
+        raise ValueError("expected a 3-D array")
+    n0, n1, n2 = x.shape
+    out = np.empty((n0, n1, n2 // 2 + 1), dtype=np.complex128)
+    _check(_load().orc_r2c_3d(x.ctypes.data, out.ctypes.data, n0, n1, n2,
+                              METHODS[method], _threads(nthreads)))
+    return out
+
+
+def c2r(X, n2: int, method: str = "fft", nthreads=None) -> np.ndarray:
+    """3-D c2r of a half spectrum [n0, n1, n2//2 + 1] -> real [n0, n1, n2] (x 1/N)."""
+    X = _c128(X)
+    n0, n1, nh = X.shape
+    if nh != n2 // 2 + 1:
+        raise ValueError("half-spectrum width must be n2//2 + 1")
+    out = np.empty((n0, n1, n2), dtype=np.float64)
+    _check(_load().orc_c2r_3d(X.ctypes.data, out.ctypes.data, n0, n1, n2,
+                              METHODS[method], _threads(nthreads)))
+    return out
+
+
+def dft_axis(x, axis: int, sign: int = -1, method: str = "fft", nthreads=None) -> np.ndarray:
+    """Unscaled 1-D DFT of every line of a complex N-d array along ``axis``."""
+    x = _c128(x).copy()
+    shape = x.shape
+    axis = axis % x.ndim
+    outer = int(np.prod(shape[:axis], dtype=np.int64))
+    inner = int(np.prod(shape[axis + 1:], dtype=np.int64))
+    _check(_load().orc_dft_axis(x.ctypes.data, outer, shape[axis], inner, int(sign),
+                                METHODS[method], _threads(nthreads)))
+    return x
+
+
+def rel_l2(y, ref) -> float:
+    """||y - ref||_2 / ||ref||_2 accumulated in float64 (long double where numpy has it)."""
+    y = np.asarray(y)
+    ref = np.asarray(ref)
+    acc = np.longdouble
+    d = (y.astype(np.complex128) - ref.astype(np.complex128)).ravel()
+    num = np.sum(d.real.astype(acc) ** 2 + d.imag.astype(acc) ** 2)
+    r = ref.astype(np.complex128).ravel()
+    den = np.sum(r.real.astype(acc) ** 2 + r.imag.astype(acc) ** 2)
+    if den == 0:
+        return float(np.sqrt(num))
+    return float(np.sqrt(num / den))
