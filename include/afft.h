@@ -1,0 +1,162 @@
+/*
+ * afft.h -- C ABI of a single-GPU (GB300, sm_103a) 3-D FFT library.
+ *
+ * What it computes.  AccFFT (Gholami, Hill, Malhotra, Biros, arXiv 1506.07933)
+ * describes a library that, given an N0 x N1 x N2 array, computes its Fourier
+ * transform (Section 1, "Contributions"), R2C, C2C and C2R, in single and
+ * double precision, by batched 1-D FFTs along one axis at a time with
+ * transposes between them (Algorithm 1, pencil decomposition).  On one GPU the
+ * process grid is P0 = P1 = 1 and the paper's all-to-all exchanges become data
+ * movement inside the device; this library computes the same result:
+ *
+ *   forward   X[k0,k1,k2] = sum_j x[j0,j1,j2] exp(-2 pi i (j0k0/N0 + j1k1/N1 + j2k2/N2))
+ *   backward  x[j]        = (1/N) sum_k X[k] exp(+2 pi i (...)),  N = N0 N1 N2
+ *
+ * The forward transform is unscaled and the backward one carries the full
+ * 1/N normalisation (Section 2, footnote 2), so backward(forward(x)) = x.
+ * The exponent sign is not printed in the paper; the one above is that of
+ * the FFT libraries the paper builds on.
+ *
+ * Layout.  Row-major [n0][n1][n2], n[0] slowest and n[2] contiguous: the
+ * paper's N0, N1, N2 (Section 2 notation).  The frequency-domain array keeps
+ * the same axis order as the spatial one (Section 2: AccFFT keeps the xyz
+ * layout in frequency space, no transposed-out option), bins in natural
+ * order 0..n-1.  Complex values are interleaved {re, im}: float2 for
+ * AFFT_F32, double2 for AFFT_F64.
+ *   AFFT_C2C: in and out are n0*n1*n2 complex.
+ *   AFFT_R2C: forward in = n0*n1*n2 real, out = n0*n1*(n2/2+1) complex (the
+ *             halved axis is the contiguous one, transformed first as in
+ *             Algorithm 1); backward (c2r) is the reverse.  n2 must be even.
+ *             c2r reads only the real parts of bins k2 = 0 and k2 = n2/2.
+ *
+ * Ownership and execution.  The caller owns `in` and `out` (device pointers,
+ * e.g. from torch tensors).  The plan owns its device twiddle tables and
+ * workspace, allocated in afft_plan_create and freed in afft_plan_destroy;
+ * execute allocates nothing.  `in` is never modified (c2r included).
+ * Transforms are out-of-place: in == out returns AFFT_ERR_INPLACE, and the
+ * two buffers must not overlap.  Execute enqueues kernels on the given
+ * stream (a cudaStream_t, NULL = legacy default stream) and returns without
+ * synchronising.  A plan may be used by one stream at a time; plans are
+ * independent of each other.  A plan belongs to the device that was
+ * current when it was created.
+ *
+ * Errors.  Every function returns an int status (AFFT_OK = 0).  Nothing
+ * throws across this boundary and nothing aborts.  A CUDA launch error is
+ * returned as AFFT_ERR_CUDA by the call that launched; an asynchronous fault
+ * surfaces at the next CUDA call on that device.
+ */
+#ifndef AFFT_H
+#define AFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afft_plan afft_plan;
+
+/* Transform kinds (AccFFT Section 1: R2C, C2C, C2R).  An R2C plan runs r2c
+ * forward and c2r backward. */
+enum { AFFT_C2C = 0, AFFT_R2C = 1 };
+
+/* Precisions (AccFFT Section 1: single and double precision).
+ * AFFT_F32_SPLIT is reserved for a split-precision tensor-core path and is
+ * rejected with AFFT_ERR_UNSUPPORTED by this version. */
+enum { AFFT_F32 = 0, AFFT_F64 = 1, AFFT_F32_SPLIT = 2 };
+
+enum {
+    AFFT_OK = 0,
+    AFFT_ERR_NULL = 1,        /* a required pointer argument is NULL           */
+    AFFT_ERR_SIZE = 2,        /* some n[i] < 1, or has a prime factor > 5      */
+    AFFT_ERR_R2C_ODD = 3,     /* R2C plan with odd n[2]                        */
+    AFFT_ERR_KIND = 4,        /* kind is not AFFT_C2C or AFFT_R2C              */
+    AFFT_ERR_PRECISION = 5,   /* precision is not one of the enum values       */
+    AFFT_ERR_NOMEM = 6,       /* device or host allocation failed in create    */
+    AFFT_ERR_INPLACE = 7,     /* in == out                                     */
+    AFFT_ERR_CUDA = 8,        /* a CUDA call or kernel launch failed           */
+    AFFT_ERR_UNSUPPORTED = 9  /* valid request this version does not implement */
+};
+
+/*
+ * Create a plan for an n[0] x n[1] x n[2] transform (AccFFT Section 1: the
+ * library takes an N0 x N1 x N2 array).  Factors each axis into radix
+ * 16/8/4/2/3/5 passes (the Cooley-Tukey reduction of Section 2), computes
+ * the twiddle tables in FP64 on the current device, and allocates the
+ * workspace.  Each n[i] must be >= 1 with prime factors in {2, 3, 5}, and
+ * at most 4096 (longer lines return AFFT_ERR_UNSUPPORTED).
+ *   out:       receives the plan (set to NULL on failure).
+ *   n:         host array of 3 sizes, slowest first.
+ *   kind:      AFFT_C2C or AFFT_R2C.
+ *   precision: AFFT_F32 or AFFT_F64.
+ * Synchronises the current device once (twiddle upload) before returning.
+ */
+int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precision);
+
+/*
+ * Forward transform (Algorithm 1, left column): 1-D FFTs along N2, then N1,
+ * then N0, unscaled.  C2C: in, out complex [n0][n1][n2].  R2C: in real
+ * [n0][n1][n2], out complex [n0][n1][n2/2+1].  Device pointers; stream is a
+ * cudaStream_t (may be NULL).  Asynchronous.
+ */
+int afft_execute_forward(afft_plan *p, const void *in, void *out, void *cuda_stream);
+
+/*
+ * Backward transform (Algorithm 1, right column): inverse 1-D FFTs along
+ * N0, then N1, then N2, and x 1/N folded into the last store (Section 2,
+ * footnote 2).  C2C: complex -> complex.  R2C plan: complex [n0][n1][n2/2+1]
+ * -> real [n0][n1][n2] (c2r; the half spectrum is treated as Hermitian
+ * along k2).  `in` is not modified.  Asynchronous.
+ */
+int afft_execute_backward(afft_plan *p, const void *in, void *out, void *cuda_stream);
+
+/*
+ * The same transforms with the data in host memory: copies host_in into the
+ * caller's device buffer dev_in, runs the transform into dev_out, and copies
+ * dev_out back to host_out, all enqueued on the stream (pinned host memory
+ * makes the copies asynchronous; pageable memory makes them synchronous).
+ * The caller owns all four buffers; sizes are those of the device variant.
+ * dev_in and dev_out must not overlap.  Returns before the copy back completes
+ * when host_out is pinned: synchronise the stream before reading it.
+ */
+int afft_execute_forward_host(afft_plan *p, const void *host_in, void *host_out,
+                              void *dev_in, void *dev_out, void *cuda_stream);
+int afft_execute_backward_host(afft_plan *p, const void *host_in, void *host_out,
+                               void *dev_in, void *dev_out, void *cuda_stream);
+
+/* Destroy a plan and free its device memory.  NULL is a no-op (AFFT_OK).
+ * Synchronises the plan's device before freeing. */
+int afft_plan_destroy(afft_plan *p);
+
+/* Bytes of device workspace the plan holds (0 for a NULL plan). */
+size_t afft_plan_workspace_bytes(const afft_plan *p);
+
+/* Bytes of the input / output buffer of the forward transform (0 for NULL).
+ * The backward transform swaps them. */
+size_t afft_plan_input_bytes(const afft_plan *p);
+size_t afft_plan_output_bytes(const afft_plan *p);
+
+/* Number of kernel launches one execute_forward / execute_backward makes. */
+int afft_plan_launches(const afft_plan *p, int backward);
+
+/* Static description of a status code. */
+const char *afft_status_string(int status);
+
+/*
+ * Synthetic input generator (not part of the transform): fills `count`
+ * interleaved complex values at dev_out with U[-1, 1) numbers from the
+ * counter-based splitmix64 generator (Steele, Lea, Flood 2014):
+ *   value(i, part) = (splitmix64(seed ^ (2 i + part)) >> 40) * 2^-24 * 2 - 1,
+ * part 0 = re, 1 = im, complex index i = 0..count-1.  precision AFFT_F32
+ * writes float2, AFFT_F64 writes double2 (same values, exact in both).
+ * Asynchronous on the stream.
+ */
+int afft_fill_uniform(void *dev_out, int64_t count, uint64_t seed, int precision,
+                      void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFFT_H */

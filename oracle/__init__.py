@@ -55,8 +55,9 @@ def _load():
         lib.orc_dft_axis.argtypes = [dp, i64, i64, i64, c_int, c_int, c_int]
         lib.orc_c2c_3d.argtypes = [dp, dp, i64, i64, i64, c_int, c_int, c_int]
         lib.orc_r2c_3d.argtypes = [dp, dp, i64, i64, i64, c_int, c_int]
+        lib.orc_dft_bins.argtypes = [dp, c_int, i64, i64, i64, dp, i64, dp, c_int]
         lib.orc_c2r_3d.argtypes = [dp, dp, i64, i64, i64, c_int, c_int]
-        for f in (lib.orc_dft_axis, lib.orc_c2c_3d, lib.orc_r2c_3d, lib.orc_c2r_3d):
+        for f in (lib.orc_dft_axis, lib.orc_c2c_3d, lib.orc_r2c_3d, lib.orc_c2r_3d, lib.orc_dft_bins):
             f.restype = c_int
         lib.orc_max_threads.restype = c_int
         _lib = lib
@@ -128,15 +129,34 @@ def dft_axis(x, axis: int, sign: int = -1, method: str = "fft", nthreads=None) -
     return x
 
 
+def dft_bins(x, ks, nthreads=None) -> np.ndarray:
+    """Forward 3-D DFT bins X[k] for the (k0, k1, k2) rows of ``ks``, by the definition.
+
+    ``x`` is a real or complex [n0, n1, n2] array; costs O(N) per bin.
+    """
+    is_real = not np.iscomplexobj(x)
+    x = np.ascontiguousarray(x, dtype=np.float64 if is_real else np.complex128)
+    ks = np.ascontiguousarray(np.asarray(ks, dtype=np.int64).reshape(-1, 3))
+    n0, n1, n2 = x.shape
+    out = np.empty(len(ks), dtype=np.complex128)
+    _check(_load().orc_dft_bins(x.ctypes.data, int(is_real), n0, n1, n2, ks.ctypes.data, len(ks),
+                                out.ctypes.data, _threads(nthreads)))
+    return out
+
+
 def rel_l2(y, ref) -> float:
-    """||y - ref||_2 / ||ref||_2 accumulated in float64 (long double where numpy has it)."""
-    y = np.asarray(y)
-    ref = np.asarray(ref)
-    acc = np.longdouble
-    d = (y.astype(np.complex128) - ref.astype(np.complex128)).ravel()
-    num = np.sum(d.real.astype(acc) ** 2 + d.imag.astype(acc) ** 2)
-    r = ref.astype(np.complex128).ravel()
-    den = np.sum(r.real.astype(acc) ** 2 + r.imag.astype(acc) ** 2)
+    """||y - ref||_2 / ||ref||_2 with float64 pairwise sums, in chunks of 2**24 values."""
+    y = np.asarray(y).ravel()
+    ref = np.asarray(ref).ravel()
+    if y.shape != ref.shape:
+        raise ValueError("shape mismatch %s vs %s" % (y.shape, ref.shape))
+    num = den = 0.0
+    step = 1 << 24
+    for i in range(0, ref.size, step):
+        r = ref[i:i + step].astype(np.complex128)
+        d = y[i:i + step].astype(np.complex128) - r
+        num += float(np.sum(d.real * d.real + d.imag * d.imag))
+        den += float(np.sum(r.real * r.real + r.imag * r.imag))
     if den == 0:
         return float(np.sqrt(num))
     return float(np.sqrt(num / den))

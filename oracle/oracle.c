@@ -304,6 +304,76 @@ int orc_c2r_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2
     return ORC_OK;
 }
 
+/*
+ * Selected bins of the forward 3-D DFT straight from the definition, for
+ * arrays too large to transform whole on the CPU:
+ *   X[k] = sum_{j0} w0^{j0 k0} sum_{j1} w1^{j1 k1} sum_{j2} w2^{j2 k2} x[j0,j1,j2]
+ * (the same sum, grouped by axis; each unit root is looked up by its exact
+ * integer phase (j k) mod n).  in: complex (is_real = 0) or real (is_real = 1)
+ * [n0][n1][n2]; ks: nk triples (k0, k1, k2) with 0 <= ki < ni; out: nk complex.
+ */
+int orc_dft_bins(const double *in, int is_real, int64_t n0, int64_t n1, int64_t n2,
+                 const int64_t *ks, int64_t nk, double *out, int nthreads)
+{
+    if (!in || !ks || !out || bad_dims(n0, n1, n2) || nk < 0) return ORC_ERR_ARG;
+    for (int64_t b = 0; b < nk; ++b)
+        if (ks[3 * b] < 0 || ks[3 * b] >= n0 || ks[3 * b + 1] < 0 || ks[3 * b + 1] >= n1 ||
+            ks[3 * b + 2] < 0 || ks[3 * b + 2] >= n2)
+            return ORC_ERR_ARG;
+    for (int64_t b = 0; b < nk; ++b) {
+        const int64_t k0 = ks[3 * b], k1 = ks[3 * b + 1], k2 = ks[3 * b + 2];
+        cplx *w0 = (cplx *)malloc(sizeof(cplx) * (size_t)n0);
+        cplx *w1 = (cplx *)malloc(sizeof(cplx) * (size_t)n1);
+        cplx *w2 = (cplx *)malloc(sizeof(cplx) * (size_t)n2);
+        if (!w0 || !w1 || !w2) { free(w0); free(w1); free(w2); return ORC_ERR_NOMEM; }
+        for (int64_t j = 0; j < n0; ++j) {
+            long double a = ORC_TWO_PI * (long double)((j * k0) % n0) / (long double)n0;
+            w0[j].re = (double)cosl(a); w0[j].im = -(double)sinl(a);
+        }
+        for (int64_t j = 0; j < n1; ++j) {
+            long double a = ORC_TWO_PI * (long double)((j * k1) % n1) / (long double)n1;
+            w1[j].re = (double)cosl(a); w1[j].im = -(double)sinl(a);
+        }
+        for (int64_t j = 0; j < n2; ++j) {
+            long double a = ORC_TWO_PI * (long double)((j * k2) % n2) / (long double)n2;
+            w2[j].re = (double)cosl(a); w2[j].im = -(double)sinl(a);
+        }
+        double sr = 0.0, si = 0.0;
+#ifdef _OPENMP
+        if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for num_threads(nthreads) reduction(+ : sr, si) schedule(static)
+#endif
+        for (int64_t j0 = 0; j0 < n0; ++j0) {
+            double ar = 0.0, ai = 0.0;
+            for (int64_t j1 = 0; j1 < n1; ++j1) {
+                double br = 0.0, bi = 0.0;
+                const int64_t base = (j0 * n1 + j1) * n2;
+                if (is_real) {
+                    const double *x = in + base;
+                    for (int64_t j2 = 0; j2 < n2; ++j2) {
+                        br += x[j2] * w2[j2].re;
+                        bi += x[j2] * w2[j2].im;
+                    }
+                } else {
+                    const cplx *x = (const cplx *)in + base;
+                    for (int64_t j2 = 0; j2 < n2; ++j2) {
+                        br += x[j2].re * w2[j2].re - x[j2].im * w2[j2].im;
+                        bi += x[j2].re * w2[j2].im + x[j2].im * w2[j2].re;
+                    }
+                }
+                ar += br * w1[j1].re - bi * w1[j1].im;
+                ai += br * w1[j1].im + bi * w1[j1].re;
+            }
+            sr += ar * w0[j0].re - ai * w0[j0].im;
+            si += ar * w0[j0].im + ai * w0[j0].re;
+        }
+        out[2 * b] = sr;
+        out[2 * b + 1] = si;
+        free(w0); free(w1); free(w2);
+    }
+    return ORC_OK;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

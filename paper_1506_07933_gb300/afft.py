@@ -1,0 +1,256 @@
+"""ctypes binding of libafft.so -- argument marshalling only.
+
+Every step of the transform runs in the CUDA library; this module checks
+tensor shapes, dtypes and devices, passes raw pointers and the current CUDA
+stream through the C ABI of ``include/afft.h``, and turns status codes into
+exceptions.  PyTorch provides device memory and streams.  There is no CPU
+fallback: if the library is missing or cannot be loaded, every call raises.
+
+Low-level functions carry the C names (``afft_plan_create`` and so on);
+``Plan`` wraps them for tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build.LIB
+
+C2C, R2C = 0, 1
+F32, F64, F32_SPLIT = 0, 1, 2
+KINDS = {"c2c": C2C, "r2c": R2C}
+PRECISIONS = {"f32": F32, "f64": F64, "f32_split": F32_SPLIT}
+
+STATUS = {
+    0: "AFFT_OK", 1: "AFFT_ERR_NULL", 2: "AFFT_ERR_SIZE", 3: "AFFT_ERR_R2C_ODD", 4: "AFFT_ERR_KIND",
+    5: "AFFT_ERR_PRECISION", 6: "AFFT_ERR_NOMEM", 7: "AFFT_ERR_INPLACE", 8: "AFFT_ERR_CUDA",
+    9: "AFFT_ERR_UNSUPPORTED",
+}
+
+# Every symbol include/afft.h declares.
+EXPORTS = [
+    "afft_plan_create", "afft_execute_forward", "afft_execute_backward",
+    "afft_execute_forward_host", "afft_execute_backward_host", "afft_plan_destroy",
+    "afft_plan_workspace_bytes", "afft_plan_input_bytes", "afft_plan_output_bytes",
+    "afft_plan_launches", "afft_status_string", "afft_fill_uniform",
+]
+
+_lib = None
+
+
+class AfftError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), status_string(status)))
+
+
+def load(path: str = None):
+    """Load libafft.so (in-tree).  Raises if it is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libafft.so not built (%s); run paper_1506_07933_gb300/build.py" % path)
+    lib = ctypes.CDLL(path)
+    vp, i64p, c_int, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_size_t
+    lib.afft_plan_create.argtypes = [ctypes.POINTER(vp), i64p, c_int, c_int]
+    lib.afft_execute_forward.argtypes = [vp, vp, vp, vp]
+    lib.afft_execute_backward.argtypes = [vp, vp, vp, vp]
+    lib.afft_execute_forward_host.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.afft_execute_backward_host.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.afft_plan_destroy.argtypes = [vp]
+    for f in ("afft_plan_workspace_bytes", "afft_plan_input_bytes", "afft_plan_output_bytes"):
+        getattr(lib, f).argtypes = [vp]
+        getattr(lib, f).restype = sz
+    lib.afft_plan_launches.argtypes = [vp, c_int]
+    lib.afft_status_string.argtypes = [c_int]
+    lib.afft_status_string.restype = ctypes.c_char_p
+    lib.afft_fill_uniform.argtypes = [vp, ctypes.c_int64, ctypes.c_uint64, c_int, vp]
+    for f in ("afft_plan_create", "afft_execute_forward", "afft_execute_backward",
+              "afft_execute_forward_host", "afft_execute_backward_host", "afft_plan_destroy",
+              "afft_plan_launches", "afft_fill_uniform"):
+        getattr(lib, f).restype = c_int
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().afft_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise AfftError(status, where)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ------------------------------------------------------------------ C names --
+
+def afft_plan_create(shape, kind: int, precision: int) -> ctypes.c_void_p:
+    n = (ctypes.c_int64 * 3)(*[int(s) for s in shape])
+    p = ctypes.c_void_p()
+    _check(load().afft_plan_create(ctypes.byref(p), n, int(kind), int(precision)), "afft_plan_create")
+    return p
+
+
+def afft_execute_forward(plan, in_ptr: int, out_ptr: int, stream: int) -> None:
+    _check(load().afft_execute_forward(plan, in_ptr, out_ptr, stream), "afft_execute_forward")
+
+
+def afft_execute_backward(plan, in_ptr: int, out_ptr: int, stream: int) -> None:
+    _check(load().afft_execute_backward(plan, in_ptr, out_ptr, stream), "afft_execute_backward")
+
+
+def afft_execute_forward_host(plan, host_in, host_out, dev_in, dev_out, stream: int) -> None:
+    _check(load().afft_execute_forward_host(plan, host_in, host_out, dev_in, dev_out, stream),
+           "afft_execute_forward_host")
+
+
+def afft_execute_backward_host(plan, host_in, host_out, dev_in, dev_out, stream: int) -> None:
+    _check(load().afft_execute_backward_host(plan, host_in, host_out, dev_in, dev_out, stream),
+           "afft_execute_backward_host")
+
+
+def afft_plan_destroy(plan) -> None:
+    _check(load().afft_plan_destroy(plan), "afft_plan_destroy")
+
+
+def afft_fill_uniform(ptr: int, count: int, seed: int, precision: int, stream: int) -> None:
+    _check(load().afft_fill_uniform(ptr, int(count), int(seed), int(precision), stream),
+           "afft_fill_uniform")
+
+
+# --------------------------------------------------------------- tensor API --
+
+_CDT = {F32: torch.complex64, F64: torch.complex128}
+_RDT = {F32: torch.float32, F64: torch.float64}
+
+
+class Plan:
+    """A resident 3-D FFT plan: ``Plan((n0, n1, n2), "c2c" | "r2c", "f32" | "f64")``.
+
+    ``forward(x)``: unscaled forward transform (c2c: complex -> complex;
+    r2c: real [n0, n1, n2] -> complex [n0, n1, n2 // 2 + 1]).
+    ``backward(X)``: inverse scaled by 1/N (c2c, or c2r for an r2c plan).
+    Tensors must be contiguous, on the plan's device, of the plan's dtype.
+    Calls are asynchronous on the current (or given) stream.
+    """
+
+    def __init__(self, shape, kind="c2c", precision="f32"):
+        self.shape = tuple(int(s) for s in shape)
+        self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._p = afft_plan_create(self.shape, self.kind, self.precision)
+        lib = load()
+        self.workspace_bytes = lib.afft_plan_workspace_bytes(self._p)
+        self.input_bytes = lib.afft_plan_input_bytes(self._p)
+        self.output_bytes = lib.afft_plan_output_bytes(self._p)
+
+    # shapes / dtypes of the forward input and output
+    @property
+    def spatial_shape(self):
+        return self.shape
+
+    @property
+    def spectral_shape(self):
+        n0, n1, n2 = self.shape
+        return (n0, n1, n2 // 2 + 1) if self.kind == R2C else self.shape
+
+    @property
+    def spatial_dtype(self):
+        return _RDT[self.precision] if self.kind == R2C else _CDT[self.precision]
+
+    @property
+    def spectral_dtype(self):
+        return _CDT[self.precision]
+
+    def launches(self, backward: bool = False) -> int:
+        return load().afft_plan_launches(self._p, int(bool(backward)))
+
+    def _check_tensor(self, t, shape, dtype, what):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("%s must be a torch.Tensor" % what)
+        if t.device != self.device:
+            raise ValueError("%s must be on %s, got %s" % (what, self.device, t.device))
+        if t.dtype != dtype:
+            raise TypeError("%s must be %s, got %s" % (what, dtype, t.dtype))
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError("%s must have shape %s, got %s" % (what, shape, tuple(t.shape)))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % what)
+
+    def forward(self, x, out=None, stream=None):
+        self._check_tensor(x, self.spatial_shape, self.spatial_dtype, "input")
+        if out is None:
+            out = torch.empty(self.spectral_shape, dtype=self.spectral_dtype, device=self.device)
+        self._check_tensor(out, self.spectral_shape, self.spectral_dtype, "output")
+        afft_execute_forward(self._p, x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def backward(self, X, out=None, stream=None):
+        self._check_tensor(X, self.spectral_shape, self.spectral_dtype, "input")
+        if out is None:
+            out = torch.empty(self.spatial_shape, dtype=self.spatial_dtype, device=self.device)
+        self._check_tensor(out, self.spatial_shape, self.spatial_dtype, "output")
+        afft_execute_backward(self._p, X.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def forward_host(self, host_in, host_out, dev_in, dev_out, stream=None):
+        """Host -> device copy, forward transform, device -> host copy (one C-ABI call)."""
+        self._check_tensor(dev_in, self.spatial_shape, self.spatial_dtype, "dev_in")
+        self._check_tensor(dev_out, self.spectral_shape, self.spectral_dtype, "dev_out")
+        for t, shape, dt, w in ((host_in, self.spatial_shape, self.spatial_dtype, "host_in"),
+                                (host_out, self.spectral_shape, self.spectral_dtype, "host_out")):
+            if t.device.type != "cpu" or t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous CPU tensor %s %s" % (w, dt, shape))
+        afft_execute_forward_host(self._p, host_in.data_ptr(), host_out.data_ptr(), dev_in.data_ptr(),
+                                  dev_out.data_ptr(), _stream_handle(stream))
+
+    def backward_host(self, host_in, host_out, dev_in, dev_out, stream=None):
+        """Host -> device copy, backward transform, device -> host copy (one C-ABI call)."""
+        self._check_tensor(dev_in, self.spectral_shape, self.spectral_dtype, "dev_in")
+        self._check_tensor(dev_out, self.spatial_shape, self.spatial_dtype, "dev_out")
+        for t, shape, dt, w in ((host_in, self.spectral_shape, self.spectral_dtype, "host_in"),
+                                (host_out, self.spatial_shape, self.spatial_dtype, "host_out")):
+            if t.device.type != "cpu" or t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous CPU tensor %s %s" % (w, dt, shape))
+        afft_execute_backward_host(self._p, host_in.data_ptr(), host_out.data_ptr(), dev_in.data_ptr(),
+                                   dev_out.data_ptr(), _stream_handle(stream))
+
+    def close(self):
+        if getattr(self, "_p", None):
+            afft_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def fill_uniform(t: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
+    """Fill a contiguous complex64/complex128 CUDA tensor with the splitmix64 U[-1, 1) generator."""
+    prec = {torch.complex64: F32, torch.complex128: F64}[t.dtype]
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("fill_uniform needs a contiguous CUDA tensor")
+    afft_fill_uniform(t.data_ptr(), t.numel(), seed, prec, _stream_handle(stream))
+    return t

@@ -1,0 +1,561 @@
+// afft.cu -- plan creation, execution and the C ABI of the 3-D FFT library.
+//
+// A plan holds, for each of the three axes, the radix factorisation of its
+// line length (the Cooley-Tukey reduction of AccFFT Section 2), the twiddle
+// tables of every pass computed in FP64 on the device, and the launch shape
+// of the stage kernel.  Executing runs the three stages of Algorithm 1
+// (P0 = P1 = 1) on the caller's stream: forward N2, N1, N0; backward N0, N1,
+// N2 with the 1/N of Section 2, footnote 2 folded into the last store.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/afft.h"
+#include "afft_internal.h"
+
+using namespace afft;
+
+struct AxisPlan {
+    StageDesc desc;
+    Launch launch;
+    const KernelSet *ks;   // kernels for this line length (specialised or generic)
+    int tw_base;           // first twiddle of this axis in the plan's table; desc.tw_off is relative
+};
+
+struct afft_plan {
+    int64_t n[3];
+    int kind;
+    int precision;
+    int64_t nh;            // last-axis length of the complex array: n2 (C2C) or n2/2+1 (R2C)
+    AxisPlan ax[3];        // ax[2] transforms the contiguous axis (length n2, or n2/2 for R2C)
+    int post_off;          // R2C: offset of the w_{n2}^k table (n2/2+1 entries)
+    void *d_tw;            // twiddle tables (float2 or double2)
+    void *d_work;          // c2r workspace: n0*n1*nh complex
+    size_t work_bytes;
+    int device;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- plans ----
+
+bool factor_ok(int64_t n)
+{
+    if (n < 1) return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Radix passes for a line of n points: the power-of-two part as evenly sized
+// radix-16/8/4/2 passes, then one pass per factor 3 and 5.
+std::vector<int> radix_plan(int64_t n)
+{
+    std::vector<int> r;
+    int a = 0;
+    while (n % 2 == 0) { n /= 2; ++a; }
+    if (a > 0) {
+        const int passes = (a + 3) / 4;
+        for (int i = 0; i < passes; ++i) {
+            const int bits = a / passes + (i < a % passes ? 1 : 0);
+            r.push_back(1 << bits);
+        }
+    }
+    while (n % 3 == 0) { n /= 3; r.push_back(3); }
+    while (n % 5 == 0) { n /= 5; r.push_back(5); }
+    return r;
+}
+
+const KernelSet *lookup_kernels(int precision, int64_t n)
+{
+    const KernelSet *k = precision == AFFT_F64 ? spec_kernels_f64((int)n) : spec_kernels_f32((int)n);
+    if (k) return k;
+    return precision == AFFT_F64 ? generic_kernels_f64() : generic_kernels_f32();
+}
+
+// Fills desc for length n (with the radix sequence of the specialised kernel
+// when there is one) and appends its twiddle entries (m, L), meaning
+// exp(-2 pi i m / L), to the table lists.
+void build_desc(int64_t n, const KernelSet *ks, StageDesc &d, std::vector<int> &tm,
+                std::vector<int> &tl)
+{
+    std::memset(&d, 0, sizeof d);
+    d.n = (int)n;
+    const int base = (int)tm.size();
+    std::vector<int> rad;
+    if (!ks->generic) rad.assign(ks->radix, ks->radix + ks->npass);
+    else rad = radix_plan(n);
+    d.npass = (int)rad.size();
+    int ns = 1;
+    for (int p = 0; p < d.npass; ++p) {
+        const int R = rad[p];
+        d.radix[p] = R;
+        d.ns[p] = ns;
+        d.tw_off[p] = (int)tm.size() - base;
+        if (ns > 1) {
+            for (int k = 0; k < ns; ++k)
+                for (int r = 1; r < R; ++r) {
+                    tm.push_back((int)(((long long)r * k) % ((long long)R * ns)));
+                    tl.push_back(R * ns);
+                }
+        }
+        ns *= R;
+    }
+}
+
+int required_threads(const StageDesc &d, int lines)
+{
+    long long req = lines;  // copy path (n == 1)
+    for (int p = 0; p < d.npass; ++p) {
+        const long long bf = (long long)lines * (d.n / d.radix[p]);
+        const int per = bmax_for_radix(d.radix[p]);
+        req = std::max(req, (bf + per - 1) / per);
+    }
+    return (int)std::max(32LL, (req + 31) / 32 * 32);
+}
+
+int ilog2(int v)
+{
+    int l = 0;
+    while ((1 << (l + 1)) <= v) ++l;
+    return l;
+}
+
+// Strided stage: `lines` adjacent columns per CTA, 128-byte rows when possible.
+bool shape_strided(const StageDesc &d, long long outer, long long W, size_t elem, int max_threads,
+                   size_t max_smem, Launch &L)
+{
+    int lines = (int)(128 / elem);
+    while (lines > 1 && lines / 2 >= W) lines /= 2;  // narrow arrays: no idle columns
+    for (;;) {
+        const int thr = required_threads(d, lines);
+        const size_t smem = (size_t)d.n * lines * elem;
+        if (thr <= max_threads && smem <= max_smem) {
+            L.lines = lines;
+            L.log2_lines = ilog2(lines);
+            L.threads = thr;
+            L.smem = smem;
+            L.tiles_per_outer = (W + lines - 1) / lines;
+            L.blocks = outer * L.tiles_per_outer;
+            return L.blocks > 0 && L.blocks < (1LL << 31);
+        }
+        if (lines == 1) return false;
+        lines /= 2;
+    }
+}
+
+// Contiguous stage: whole lines, about `target` complex points per CTA.
+bool shape_contig(const StageDesc &d, long long nlines, size_t elem, int max_threads, size_t max_smem,
+                  Launch &L)
+{
+    const int target = elem == 8 ? 4096 : 2048;
+    int lines = std::max(1, target / std::max(1, d.n));
+    lines = (int)std::min<long long>(lines, std::max(1LL, nlines));
+    const int row = (int)(128 / elem);
+    for (;;) {
+        const int thr = required_threads(d, lines);
+        const size_t pts = ((size_t)lines * d.n + row - 1) / row * row;
+        const size_t smem = pts * elem;
+        if (thr <= max_threads && smem <= max_smem) {
+            L.lines = lines;
+            L.log2_lines = 0;
+            L.threads = thr;
+            L.smem = smem;
+            L.tiles_per_outer = 1;
+            L.blocks = (nlines + lines - 1) / lines;
+            return L.blocks > 0 && L.blocks < (1LL << 31);
+        }
+        if (lines == 1) return false;
+        lines = (lines + 1) / 2;
+    }
+}
+
+// ------------------------------------------------------------- twiddles ----
+
+// Entry i of the table is exp(-2 pi i m_i / L_i), evaluated in FP64 from the
+// exact integer ratio (m reduced to (-L/2, L/2] so the argument of sincospi
+// is at most 1 in magnitude), then rounded to the table's precision.
+template <typename V>
+__global__ void k_twiddles(const int *__restrict__ m, const int *__restrict__ L, V *out, int count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int mm = m[i];
+    const int ll = L[i];
+    if (2 * mm > ll) mm -= ll;
+    double s, c;
+    sincospi(2.0 * (double)mm / (double)ll, &s, &c);
+    V v;
+    v.x = (decltype(v.x))c;
+    v.y = (decltype(v.y))(-s);
+    out[i] = v;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014) as a counter-based hash.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    unsigned long long z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_fill_uniform(T *out, long long count, unsigned long long seed)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * count; i += stride) {
+        // i = 2 * (complex index) + part
+        const unsigned long long h = splitmix64(seed ^ (unsigned long long)i);
+        out[i] = (T)((double)(h >> 40) * (1.0 / 16777216.0) * 2.0 - 1.0);
+    }
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? AFFT_OK : AFFT_ERR_CUDA; }
+
+size_t cplx_size(int precision) { return precision == AFFT_F64 ? 16 : 8; }
+size_t real_size(int precision) { return precision == AFFT_F64 ? 8 : 4; }
+
+template <typename V>
+int upload_twiddles(afft_plan *p, const std::vector<int> &tm, const std::vector<int> &tl)
+{
+    const int count = (int)tm.size();
+    if (count == 0) return AFFT_OK;
+    int *d_m = nullptr;
+    cudaError_t e = cudaMalloc(&p->d_tw, sizeof(V) * count);
+    if (e != cudaSuccess) { p->d_tw = nullptr; return AFFT_ERR_NOMEM; }
+    e = cudaMalloc(&d_m, sizeof(int) * 2 * count);
+    if (e != cudaSuccess) return AFFT_ERR_NOMEM;
+    std::vector<int> both(tm);
+    both.insert(both.end(), tl.begin(), tl.end());
+    e = cudaMemcpy(d_m, both.data(), sizeof(int) * 2 * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_twiddles<V><<<(count + 255) / 256, 256>>>(d_m, d_m + count, (V *)p->d_tw, count);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_m);
+    return cuda_status(e);
+}
+
+template <typename V>
+int plan_shapes(afft_plan *p)
+{
+    const size_t elem = sizeof(V);
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if (max_smem <= 0) max_smem = 48 * 1024;
+    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh;
+    // Specialised kernels run two CTAs per SM: keep their tiles to half the SM.
+    auto budget = [&](const AxisPlan &a) -> size_t {
+        return a.ks->generic ? (size_t)max_smem : (size_t)std::min(max_smem, 112 * 1024);
+    };
+    AxisPlan &z = p->ax[2], &y = p->ax[1], &x = p->ax[0];
+    if (!shape_contig(z.desc, n0 * n1, elem, z.ks->max_threads, budget(z), z.launch))
+        return AFFT_ERR_UNSUPPORTED;
+    if (!shape_strided(y.desc, n0, nh, elem, y.ks->max_threads, budget(y), y.launch))
+        return AFFT_ERR_UNSUPPORTED;
+    if (!shape_strided(x.desc, 1, n1 * nh, elem, x.ks->max_threads, budget(x), x.launch))
+        return AFFT_ERR_UNSUPPORTED;
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < KS_COUNT; ++k) {
+            const cudaError_t e = cudaFuncSetAttribute(p->ax[a].ks->fn[k],
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+            if (e != cudaSuccess) return AFFT_ERR_CUDA;
+        }
+    return AFFT_OK;
+}
+
+// --------------------------------------------------------------- execute ---
+
+cudaError_t launch(const AxisPlan &a, int which, void **args, cudaStream_t s)
+{
+    const Launch &L = a.launch;
+    return cudaLaunchKernel(a.ks->fn[which], dim3((unsigned)L.blocks), dim3(L.threads), args, L.smem, s);
+}
+
+template <typename V>
+cudaError_t strided(const AxisPlan &a, const V *in, V *out, const V *tw, long long W, int backward,
+                    cudaStream_t s)
+{
+    StageDesc d = a.desc;
+    tw += a.tw_base;
+    long long tpo = a.launch.tiles_per_outer;
+    int lg = a.launch.log2_lines;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&tw, (void *)&W, (void *)&tpo, (void *)&lg};
+    return launch(a, backward ? KS_STRIDED_BWD : KS_STRIDED_FWD, args, s);
+}
+
+template <typename V>
+cudaError_t contig(const AxisPlan &a, const V *in, V *out, const V *tw, long long nlines, int backward,
+                   double scale, cudaStream_t s)
+{
+    using T = decltype(V().x);
+    StageDesc d = a.desc;
+    tw += a.tw_base;
+    int lines = a.launch.lines;
+    T sc = (T)scale;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&tw, (void *)&nlines, (void *)&lines, (void *)&sc};
+    return launch(a, backward ? KS_CONTIG_BWD : KS_CONTIG_FWD, args, s);
+}
+
+template <typename V, typename T>
+cudaError_t r2c(const AxisPlan &a, const T *in, V *out, const V *tw, const V *post, long long nlines,
+                cudaStream_t s)
+{
+    StageDesc d = a.desc;
+    tw += a.tw_base;
+    int lines = a.launch.lines;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&tw, (void *)&post, (void *)&nlines, (void *)&lines};
+    return launch(a, KS_R2C, args, s);
+}
+
+template <typename V, typename T>
+cudaError_t c2r(const AxisPlan &a, const V *in, T *out, const V *tw, const V *post, long long nlines,
+                double scale, cudaStream_t s)
+{
+    StageDesc d = a.desc;
+    tw += a.tw_base;
+    int lines = a.launch.lines;
+    T sc = (T)scale;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&tw, (void *)&post, (void *)&nlines,
+                    (void *)&lines, (void *)&sc};
+    return launch(a, KS_C2R, args, s);
+}
+
+template <typename V>
+int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
+{
+    using T = decltype(V().x);
+    const V *tw = (const V *)p->d_tw;
+    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh;
+    V *o = (V *)out;
+    cudaError_t e;
+    if (p->kind == AFFT_C2C) e = contig<V>(p->ax[2], (const V *)in, o, tw, n0 * n1, 0, 1.0, s);
+    else e = r2c<V, T>(p->ax[2], (const T *)in, o, tw, tw + p->post_off, n0 * n1, s);
+    if (e != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n1 > 1 && (e = strided<V>(p->ax[1], o, o, tw, nh, 0, s)) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n0 > 1 && (e = strided<V>(p->ax[0], o, o, tw, n1 * nh, 0, s)) != cudaSuccess) return AFFT_ERR_CUDA;
+    return AFFT_OK;
+}
+
+template <typename V>
+int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
+{
+    using T = decltype(V().x);
+    const V *tw = (const V *)p->d_tw;
+    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh;
+    const double scale = 1.0 / ((double)p->n[0] * (double)p->n[1] * (double)p->n[2]);
+    // C2C works in `out`; c2r works in the plan's workspace and writes real `out` last.
+    V *buf = p->kind == AFFT_C2C ? (V *)out : (V *)p->d_work;
+    cudaError_t e = strided<V>(p->ax[0], (const V *)in, buf, tw, n1 * nh, 1, s);
+    if (e != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n1 > 1 && (e = strided<V>(p->ax[1], buf, buf, tw, nh, 1, s)) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (p->kind == AFFT_C2C) e = contig<V>(p->ax[2], buf, (V *)out, tw, n0 * n1, 1, scale, s);
+    else e = c2r<V, T>(p->ax[2], buf, (T *)out, tw, tw + p->post_off, n0 * n1, scale, s);
+    return e == cudaSuccess ? AFFT_OK : AFFT_ERR_CUDA;
+}
+
+size_t in_bytes(const afft_plan *p)
+{
+    const size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+    return p->kind == AFFT_C2C ? N * cplx_size(p->precision) : N * real_size(p->precision);
+}
+size_t out_bytes(const afft_plan *p)
+{
+    return (size_t)p->n[0] * p->n[1] * p->nh * cplx_size(p->precision);
+}
+
+bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + nb && y < x + na;
+}
+
+int check_exec(afft_plan *p, const void *in, void *out, int backward)
+{
+    if (!p || !in || !out) return AFFT_ERR_NULL;
+    if (in == out) return AFFT_ERR_INPLACE;
+    const size_t ni = backward ? out_bytes(p) : in_bytes(p);
+    const size_t no = backward ? in_bytes(p) : out_bytes(p);
+    if (overlaps(in, ni, out, no)) return AFFT_ERR_INPLACE;
+    return AFFT_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI ===
+
+extern "C" {
+
+const char *afft_status_string(int status)
+{
+    switch (status) {
+    case AFFT_OK: return "ok";
+    case AFFT_ERR_NULL: return "null pointer argument";
+    case AFFT_ERR_SIZE: return "size must be >= 1 with prime factors 2, 3, 5 only";
+    case AFFT_ERR_R2C_ODD: return "r2c/c2r needs an even last dimension";
+    case AFFT_ERR_KIND: return "unknown transform kind";
+    case AFFT_ERR_PRECISION: return "unknown precision";
+    case AFFT_ERR_NOMEM: return "out of memory";
+    case AFFT_ERR_INPLACE: return "in-place or overlapping buffers are not supported";
+    case AFFT_ERR_CUDA: return "CUDA error";
+    case AFFT_ERR_UNSUPPORTED: return "not supported by this version";
+    default: return "unknown status";
+    }
+}
+
+int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precision)
+{
+    if (!out) return AFFT_ERR_NULL;
+    *out = nullptr;
+    if (!n) return AFFT_ERR_NULL;
+    if (kind != AFFT_C2C && kind != AFFT_R2C) return AFFT_ERR_KIND;
+    if (precision != AFFT_F32 && precision != AFFT_F64 && precision != AFFT_F32_SPLIT)
+        return AFFT_ERR_PRECISION;
+    for (int i = 0; i < 3; ++i)
+        if (!factor_ok(n[i])) return AFFT_ERR_SIZE;
+    if (kind == AFFT_R2C && n[2] % 2 != 0) return AFFT_ERR_R2C_ODD;
+    if (precision == AFFT_F32_SPLIT) return AFFT_ERR_UNSUPPORTED;
+    const int64_t zlen = kind == AFFT_R2C ? n[2] / 2 : n[2];
+    if (n[0] > kMaxLine || n[1] > kMaxLine || zlen > kMaxLine) return AFFT_ERR_UNSUPPORTED;
+
+    afft_plan *p = new (std::nothrow) afft_plan;
+    if (!p) return AFFT_ERR_NOMEM;
+    std::memset(p, 0, sizeof *p);
+    for (int i = 0; i < 3; ++i) p->n[i] = n[i];
+    p->kind = kind;
+    p->precision = precision;
+    p->nh = kind == AFFT_R2C ? n[2] / 2 + 1 : n[2];
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return AFFT_ERR_CUDA;
+    }
+
+    std::vector<int> tm, tl;
+    const int64_t len[3] = {n[0], n[1], zlen};
+    for (int a = 0; a < 3; ++a) {
+        p->ax[a].ks = lookup_kernels(precision, len[a]);
+        p->ax[a].tw_base = (int)tm.size();
+        build_desc(len[a], p->ax[a].ks, p->ax[a].desc, tm, tl);
+    }
+    p->post_off = (int)tm.size();
+    if (kind == AFFT_R2C) {
+        for (int64_t k = 0; k <= n[2] / 2; ++k) {
+            tm.push_back((int)k);
+            tl.push_back((int)n[2]);
+        }
+    }
+
+    int st = precision == AFFT_F64 ? plan_shapes<double2>(p) : plan_shapes<float2>(p);
+    if (st == AFFT_OK)
+        st = precision == AFFT_F64 ? upload_twiddles<double2>(p, tm, tl) : upload_twiddles<float2>(p, tm, tl);
+    if (st == AFFT_OK && kind == AFFT_R2C) {
+        p->work_bytes = (size_t)n[0] * n[1] * p->nh * cplx_size(precision);
+        if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) {
+            p->d_work = nullptr;
+            p->work_bytes = 0;
+            st = AFFT_ERR_NOMEM;
+        }
+    }
+    if (st != AFFT_OK) {
+        cudaGetLastError();  // clear a sticky launch error from the failed step
+        afft_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return AFFT_OK;
+}
+
+int afft_execute_forward(afft_plan *p, const void *in, void *out, void *stream)
+{
+    const int st = check_exec(p, in, out, 0);
+    if (st != AFFT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->precision == AFFT_F64 ? run_forward<double2>(p, in, out, s) : run_forward<float2>(p, in, out, s);
+}
+
+int afft_execute_backward(afft_plan *p, const void *in, void *out, void *stream)
+{
+    const int st = check_exec(p, in, out, 1);
+    if (st != AFFT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->precision == AFFT_F64 ? run_backward<double2>(p, in, out, s)
+                                    : run_backward<float2>(p, in, out, s);
+}
+
+static int execute_host(afft_plan *p, const void *host_in, void *host_out, void *dev_in, void *dev_out,
+                        void *stream, int backward)
+{
+    if (!p || !host_in || !host_out || !dev_in || !dev_out) return AFFT_ERR_NULL;
+    const size_t ni = backward ? out_bytes(p) : in_bytes(p);
+    const size_t no = backward ? in_bytes(p) : out_bytes(p);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(dev_in, host_in, ni, cudaMemcpyHostToDevice, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    const int st = backward ? afft_execute_backward(p, dev_in, dev_out, stream)
+                            : afft_execute_forward(p, dev_in, dev_out, stream);
+    if (st != AFFT_OK) return st;
+    if (cudaMemcpyAsync(host_out, dev_out, no, cudaMemcpyDeviceToHost, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    return AFFT_OK;
+}
+
+int afft_execute_forward_host(afft_plan *p, const void *host_in, void *host_out, void *dev_in,
+                              void *dev_out, void *stream)
+{
+    return execute_host(p, host_in, host_out, dev_in, dev_out, stream, 0);
+}
+
+int afft_execute_backward_host(afft_plan *p, const void *host_in, void *host_out, void *dev_in,
+                               void *dev_out, void *stream)
+{
+    return execute_host(p, host_in, host_out, dev_in, dev_out, stream, 1);
+}
+
+int afft_plan_destroy(afft_plan *p)
+{
+    if (!p) return AFFT_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    int st = AFFT_OK;
+    if (p->d_tw || p->d_work) {
+        if (cudaDeviceSynchronize() != cudaSuccess) st = AFFT_ERR_CUDA;
+        if (p->d_tw) cudaFree(p->d_tw);
+        if (p->d_work) cudaFree(p->d_work);
+    }
+    if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
+    delete p;
+    return st;
+}
+
+size_t afft_plan_workspace_bytes(const afft_plan *p) { return p ? p->work_bytes : 0; }
+size_t afft_plan_input_bytes(const afft_plan *p) { return p ? in_bytes(p) : 0; }
+size_t afft_plan_output_bytes(const afft_plan *p) { return p ? out_bytes(p) : 0; }
+
+int afft_plan_launches(const afft_plan *p, int backward)
+{
+    if (!p) return 0;
+    if (backward) return 2 + (p->n[1] > 1 ? 1 : 0);
+    return 1 + (p->n[1] > 1 ? 1 : 0) + (p->n[0] > 1 ? 1 : 0);
+}
+
+int afft_fill_uniform(void *dev_out, int64_t count, uint64_t seed, int precision, void *stream)
+{
+    if (!dev_out) return AFFT_ERR_NULL;
+    if (count < 0) return AFFT_ERR_SIZE;
+    if (precision != AFFT_F32 && precision != AFFT_F64) return AFFT_ERR_PRECISION;
+    if (count == 0) return AFFT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int threads = 256;
+    const long long want = (2 * count + threads - 1) / threads;
+    const unsigned blocks = (unsigned)std::min<long long>(want, 152LL * 64);
+    if (precision == AFFT_F64)
+        k_fill_uniform<double><<<blocks, threads, 0, s>>>((double *)dev_out, count, seed);
+    else
+        k_fill_uniform<float><<<blocks, threads, 0, s>>>((float *)dev_out, count, seed);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// fft_access.cuh -- tile accessors of the stage kernels.
+//
+// A tile element is addressed by (l, p): line l of the CTA's tile, position p
+// along the line.  Sources return a value (operator()(l, p)), sinks take one
+// (operator()(l, p, v)).  Global accessors read and write the caller's arrays;
+// shared-memory accessors hold the tile between radix passes.
+#pragma once
+
+#include "fft_math.cuh"
+
+namespace afft {
+
+template <typename V> __device__ __forceinline__ V czero() { return cmk<V>(0, 0); }
+
+// Shared-memory tile of a strided stage: [n][lines], one 128-byte row per
+// line position (conflict-free for line-fast thread maps).
+template <typename V> struct SmemRows {
+    V *sm;
+    int log2_lines;
+    __device__ __forceinline__ V operator()(int l, int p) const { return sm[(p << log2_lines) + l]; }
+    __device__ __forceinline__ void operator()(int l, int p, V v) const { sm[(p << log2_lines) + l] = v; }
+};
+
+// Shared-memory tile of a contiguous stage: [lines][n] with the offset
+// XOR-swizzled inside 128-byte rows, so strided pass writes spread over banks.
+template <typename V> struct SmemLines {
+    V *sm;
+    int n;
+    static constexpr int kRow = 128 / sizeof(V);
+    __device__ __forceinline__ int at(int l, int p) const
+    {
+        const int e = l * n + p;
+        return e ^ ((e / kRow) & (kRow - 1));
+    }
+    __device__ __forceinline__ V operator()(int l, int p) const { return sm[at(l, p)]; }
+    __device__ __forceinline__ void operator()(int l, int p, V v) const { sm[at(l, p)] = v; }
+};
+
+// Global columns c0 .. c0+lines-1 of a [outer][n][W] slab (strided stage).
+template <typename V> struct GlobalCols {
+    const V *base;                 // &x[o][0][c0]
+    long long W;
+    int valid;                     // columns of the tile inside the array
+    __device__ __forceinline__ V operator()(int l, int p) const
+    {
+        return l < valid ? base[(long long)p * W + l] : czero<V>();
+    }
+};
+template <typename V> struct GlobalColsOut {
+    V *base;
+    long long W;
+    int valid;
+    __device__ __forceinline__ void operator()(int l, int p, V v) const
+    {
+        if (l < valid) base[(long long)p * W + l] = v;
+    }
+};
+
+// Global contiguous lines b0 .. b0+lines-1 of length n (contiguous stage).
+template <typename V> struct GlobalLines {
+    const V *base;                 // &x[b0][0]
+    int n;                         // line stride in complex elements
+    int valid;
+    __device__ __forceinline__ V operator()(int l, int p) const
+    {
+        return l < valid ? base[l * n + p] : czero<V>();
+    }
+};
+template <typename V> struct GlobalLinesOut {
+    V *base;
+    int n;
+    int valid;
+    typename RealOf<V>::T scale;   // 1 forward, 1/N for the last backward store
+    __device__ __forceinline__ void operator()(int l, int p, V v) const
+    {
+        if (l < valid) base[l * n + p] = cscale(v, scale);
+    }
+};
+
+// c2r: builds Z[k] = E[k] + i O[k] of the half-length complex sequence from
+// the half spectrum X[0..M] of a real line of length 2M:
+//   E[k] = X[k] + conj(X[M-k]),  O[k] = (X[k] - conj(X[M-k])) w_{2M}^{+k},
+// with the imaginary parts of the self-conjugate bins X[0], X[M] dropped.
+// (The factor 1/2 of the textbook identity is folded into the 1/N scale.)
+template <typename V> struct C2RPre {
+    const V *base;                 // &X[b0][0], line stride M + 1
+    const V *post_tw;              // w_{2M}^k forward, k = 0..M
+    int M;
+    int valid;
+    __device__ __forceinline__ V operator()(int l, int k) const
+    {
+        if (l >= valid) return czero<V>();
+        const V *x = base + l * (M + 1);
+        V a = x[k];
+        V b = cconj(x[M - k]);
+        if (k == 0) {
+            a.y = 0;
+            b.y = 0;
+        }
+        const V e = cadd(a, b);
+        const V o = cmulc(csub(a, b), __ldg(post_tw + k));
+        return cmk<V>(e.x - o.y, e.y + o.x);
+    }
+};
+
+
+}  // namespace afft

@@ -1,0 +1,370 @@
+// fft_stage.cuh -- the kernels of one axis stage of the 3-D FFT.
+//
+// A stage runs batched 1-D DFTs of length n along one axis: one FFT row of
+// Algorithm 1 of AccFFT with P0 = P1 = 1.  Each CTA owns a tile of `lines`
+// lines, computes their DFTs with a Stockham autosort FFT and writes them
+// back in natural order.  One radix-R pass over a line of n points, with Ns
+// the product of the radices already applied and nb = n / R:
+//
+//   for each butterfly j < nb:  k = j mod Ns
+//     v[r] = x[j + r nb] * w_{R Ns}^{r k}                      r = 0..R-1
+//     y[(j - k) R + k + s Ns] = sum_r v[r] w_R^{r s}           s = 0..R-1
+//
+// with w_L = exp(-2 pi i / L) forward and its conjugate backward.  The
+// paper's transposes never materialise: a strided stage loads a tile of
+// adjacent columns (the paper's "pack" before the exchange is the tile load)
+// and stores it back where it came from, so the frequency-domain array keeps
+// the spatial xyz layout (the paper's local transpose back to xyz is free).
+//
+// Two implementations:
+//  * specialised kernels, one per line length in AFFT_LINE_PLANS: the radix
+//    sequence is a compile-time list, the first pass reads the tile straight
+//    from global memory and the last pass writes it straight back (both
+//    coalesced), and the passes in between exchange through shared memory;
+//  * a generic kernel for every other length: the tile is staged through
+//    shared memory and each pass is a separate (non-inlined) function chosen
+//    at run time by its radix.
+#pragma once
+
+#include "afft_internal.h"
+#include "fft_access.cuh"
+
+namespace afft {
+
+// Thread -> (line, butterfly) maps, also used as (line, position) maps by the
+// load/store loops of the generic kernel.
+struct MapLineFast {   // strided stage: consecutive threads take adjacent columns
+    int log2_lines;
+    __device__ __forceinline__ void operator()(int idx, int, int &l, int &j) const
+    {
+        l = idx & ((1 << log2_lines) - 1);
+        j = idx >> log2_lines;
+    }
+};
+struct MapButterflyFast {  // contiguous stage: consecutive threads walk along a line
+    __device__ __forceinline__ void operator()(int idx, int nb, int &l, int &j) const
+    {
+        l = idx / nb;
+        j = idx - l * nb;
+    }
+};
+
+// ------------------------------------------------------ one radix pass ------
+// Thread t handles butterflies idx = t, t + blockDim.x, ... (at most
+// bmax_for_radix(R) of them; the host sizes the CTA so that suffices).  With
+// InPlace the pass reads everything into registers, waits for the whole CTA,
+// then writes.
+
+template <int R, int S, bool InPlace, typename V, class Map, class Src, class Dst>
+__device__ __forceinline__ void radix_pass(int n, int Ns, const V *__restrict__ tw, int lines,
+                                           const Map &map, const Src &src, const Dst &dst)
+{
+    constexpr int B = bmax_for_radix(R);
+    const int nb = n / R;
+    const int total = lines * nb;
+    V v[B][R];
+    int lb[B], jb[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int idx = threadIdx.x + b * blockDim.x;
+        lb[b] = -1;
+        jb[b] = 0;
+        if (idx < total) {
+            int l, j;
+            map(idx, nb, l, j);
+            lb[b] = l;
+            jb[b] = j;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b][r] = src(l, j + r * nb);
+            if (Ns > 1) {
+                const V *t = tw + (j % Ns) * (R - 1);
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[b][r] = ctw<S>(v[b][r], __ldg(t + r - 1));
+            }
+            Dft<R, S, V>::run(v[b]);
+        }
+    }
+    if (InPlace) __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        if (lb[b] >= 0) {
+            const int j = jb[b];
+            const int k = j % Ns;
+            const int o = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst(lb[b], o + r * Ns, v[b][r]);
+        }
+    }
+}
+
+// ------------------------------------------- specialised pass sequences -----
+
+template <int... Rs> struct Seq {};
+
+template <int N, int... Rs> struct LinePlan {
+    static constexpr int n = N;
+    static constexpr int npass = sizeof...(Rs);
+    using seq = Seq<Rs...>;
+};
+
+// Runs passes Seq<R, Rest...> with Ns = product of the earlier radices and
+// TwOff = the table offset of this pass (the host lays tables out the same
+// way: Ns (R - 1) entries per pass with Ns > 1, in pass order).
+template <int S, bool First, bool LastToSmem, int N, int Ns, int TwOff, typename V, class Map,
+          class Src, class Sm, class Dst, int R, int... Rest>
+__device__ __forceinline__ void run_passes(Seq<R, Rest...>, const V *tw, int lines, const Map &map,
+                                           const Src &src, const Sm &sm, const Dst &dst)
+{
+    constexpr bool Last = sizeof...(Rest) == 0;
+    if (!First) __syncthreads();
+    if constexpr (First && Last) {
+        if constexpr (LastToSmem) radix_pass<R, S, false>(N, Ns, tw + TwOff, lines, map, src, sm);
+        else radix_pass<R, S, false>(N, Ns, tw + TwOff, lines, map, src, dst);
+    } else if constexpr (First) {
+        radix_pass<R, S, false>(N, Ns, tw + TwOff, lines, map, src, sm);
+    } else if constexpr (Last && !LastToSmem) {
+        radix_pass<R, S, false>(N, Ns, tw + TwOff, lines, map, sm, dst);
+    } else {
+        radix_pass<R, S, true>(N, Ns, tw + TwOff, lines, map, sm, sm);
+    }
+    if constexpr (!Last) {
+        constexpr int next = TwOff + (Ns > 1 ? Ns * (R - 1) : 0);
+        run_passes<S, false, LastToSmem, N, Ns * R, next>(Seq<Rest...>{}, tw, lines, map, src, sm, dst);
+    }
+}
+
+template <class P, int S, bool LastToSmem, typename V, class Map, class Src, class Sm, class Dst>
+__device__ __forceinline__ void run_plan(const V *tw, int lines, const Map &map, const Src &src,
+                                         const Sm &sm, const Dst &dst)
+{
+    if constexpr (P::npass == 0) {  // n == 1: a copy
+        for (int idx = threadIdx.x; idx < lines; idx += blockDim.x) {
+            if constexpr (LastToSmem) sm(idx, 0, src(idx, 0));
+            else dst(idx, 0, src(idx, 0));
+        }
+    } else {
+        run_passes<S, true, LastToSmem, P::n, 1, 0>(typename P::seq{}, tw, lines, map, src, sm, dst);
+    }
+}
+
+// ------------------------------------------------- generic pass sequence ----
+// One non-inlined function per (radix, direction, layout): the tile lives in
+// shared memory, so each takes only scalars and keeps its registers to itself.
+
+template <int R, int S, bool Rows, typename V>
+__device__ __noinline__ void smem_pass(V *sm, int n, int Ns, const V *tw, int lines, int log2_lines)
+{
+    if constexpr (Rows) {
+        const SmemRows<V> t{sm, log2_lines};
+        radix_pass<R, S, true>(n, Ns, tw, lines, MapLineFast{log2_lines}, t, t);
+    } else {
+        const SmemLines<V> t{sm, n};
+        radix_pass<R, S, true>(n, Ns, tw, lines, MapButterflyFast{}, t, t);
+    }
+}
+
+template <int S, bool Rows, typename V>
+__device__ __forceinline__ void smem_pass_any(int R, V *sm, int n, int Ns, const V *tw, int lines,
+                                              int log2_lines)
+{
+    switch (R) {
+    case 16: smem_pass<16, S, Rows>(sm, n, Ns, tw, lines, log2_lines); break;
+    case 8: smem_pass<8, S, Rows>(sm, n, Ns, tw, lines, log2_lines); break;
+    case 4: smem_pass<4, S, Rows>(sm, n, Ns, tw, lines, log2_lines); break;
+    case 2: smem_pass<2, S, Rows>(sm, n, Ns, tw, lines, log2_lines); break;
+    case 3: smem_pass<3, S, Rows>(sm, n, Ns, tw, lines, log2_lines); break;
+    case 5: smem_pass<5, S, Rows>(sm, n, Ns, tw, lines, log2_lines); break;
+    default: break;  // the plan emits only the radices above
+    }
+}
+
+// Generic stage body: load src -> smem, all passes in smem, store smem -> dst
+// (skipped with LastToSmem).
+template <int S, bool Rows, bool LastToSmem, typename V, class Map, class Src, class Dst>
+__device__ __forceinline__ void run_generic(const StageDesc &d, const V *tw, V *sm, int lines,
+                                            int log2_lines, const Map &map, const Src &src,
+                                            const Dst &dst)
+{
+    const int n = d.n;
+    const int total = lines * n;
+    const SmemRows<V> rows{sm, log2_lines};
+    const SmemLines<V> cols{sm, n};
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int l, p;
+        map(idx, n, l, p);
+        if constexpr (Rows) rows(l, p, src(l, p));
+        else cols(l, p, src(l, p));
+    }
+    for (int p = 0; p < d.npass; ++p) {
+        __syncthreads();
+        smem_pass_any<S, Rows>(d.radix[p], sm, n, d.ns[p], tw + d.tw_off[p], lines, log2_lines);
+    }
+    if constexpr (LastToSmem) return;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int l, p;
+        map(idx, n, l, p);
+        if constexpr (Rows) dst(l, p, rows(l, p));
+        else dst(l, p, cols(l, p));
+    }
+}
+
+// ------------------------------------------------------- kernel families ----
+
+// Specialised kernels keep two CTAs per SM resident: 512 threads x 64
+// registers for FP32, 256 x 128 for FP64.  Generic kernels use 256 threads
+// with the full register file.
+template <typename V> struct SpecThreads;
+template <> struct SpecThreads<float2> { static constexpr int value = 512; };
+template <> struct SpecThreads<double2> { static constexpr int value = 256; };
+
+template <class Plan> struct Spec {
+    static constexpr bool generic = false;
+    using plan = Plan;
+    template <typename V> static constexpr int threads() { return SpecThreads<V>::value; }
+    static constexpr int min_blocks = 2;
+};
+struct Generic {
+    static constexpr bool generic = true;
+    using plan = LinePlan<0>;
+    template <typename V> static constexpr int threads() { return 256; }
+    static constexpr int min_blocks = 1;
+};
+
+// ------------------------------------------------------------- kernels ------
+
+// Strided axis: lines run along a [outer][n][W] slab with stride W; the CTA
+// takes `lines` adjacent columns of one outer slab.
+template <class F, int S, typename V>
+__global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
+    k_strided(const V *__restrict__ in, V *out, const __grid_constant__ StageDesc d,
+              const V *__restrict__ tw, long long W, long long tiles_per_outer, int log2_lines)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sm = reinterpret_cast<V *>(smem_raw);
+    const int n = F::generic ? d.n : F::plan::n;
+    const int lines = 1 << log2_lines;
+    const long long o = blockIdx.x / tiles_per_outer;
+    const long long c0 = (blockIdx.x - o * tiles_per_outer) * lines;
+    const long long off = o * (long long)n * W + c0;
+    const int valid = (int)min((long long)lines, W - c0);
+    const GlobalCols<V> src{in + off, W, valid};
+    const GlobalColsOut<V> dst{out + off, W, valid};
+    const MapLineFast map{log2_lines};
+    if constexpr (F::generic) {
+        run_generic<S, true, false>(d, tw, sm, lines, log2_lines, map, src, dst);
+    } else {
+        const SmemRows<V> tile{sm, log2_lines};
+        run_plan<typename F::plan, S, false>(tw, lines, map, src, tile, dst);
+    }
+}
+
+// Contiguous axis, complex to complex (x scale at the store).
+template <class F, int S, typename V>
+__global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
+    k_contig(const V *__restrict__ in, V *out, const __grid_constant__ StageDesc d,
+             const V *__restrict__ tw, long long nlines, int lines, typename RealOf<V>::T scale)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sm = reinterpret_cast<V *>(smem_raw);
+    const int n = F::generic ? d.n : F::plan::n;
+    const long long b0 = (long long)blockIdx.x * lines;
+    const int valid = (int)min((long long)lines, nlines - b0);
+    const GlobalLines<V> src{in + b0 * n, n, valid};
+    const GlobalLinesOut<V> dst{out + b0 * n, n, valid, scale};
+    const MapButterflyFast map{};
+    if constexpr (F::generic) {
+        run_generic<S, false, false>(d, tw, sm, lines, 0, map, src, dst);
+    } else {
+        const SmemLines<V> tile{sm, n};
+        run_plan<typename F::plan, S, false>(tw, lines, map, src, tile, dst);
+    }
+}
+
+// Contiguous axis, real line of 2M points -> M+1 bins (forward).  The line is
+// read as M complex z[m] = x[2m] + i x[2m+1]; Z = DFT_M(z) is left in shared
+// memory and post-processed:
+//   X[k] = E[k] + w_{2M}^k O[k],  E = (Z[k] + conj Z[M-k]) / 2,
+//   O = (Z[k] - conj Z[M-k]) / (2i),  Z[M] = Z[0].
+template <class F, typename V>
+__global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
+    k_r2c(const typename RealOf<V>::T *__restrict__ in, V *out, const __grid_constant__ StageDesc d,
+          const V *__restrict__ tw, const V *__restrict__ post_tw, long long nlines, int lines)
+{
+    using T = typename RealOf<V>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sm = reinterpret_cast<V *>(smem_raw);
+    const int M = F::generic ? d.n : F::plan::n;
+    const long long b0 = (long long)blockIdx.x * lines;
+    const int valid = (int)min((long long)lines, nlines - b0);
+    const GlobalLines<V> src{reinterpret_cast<const V *>(in) + b0 * M, M, valid};
+    const SmemLines<V> tile{sm, M};
+    const MapButterflyFast map{};
+    if constexpr (F::generic) run_generic<-1, false, true>(d, tw, sm, lines, 0, map, src, tile);
+    else run_plan<typename F::plan, -1, true>(tw, lines, map, src, tile, tile);
+    __syncthreads();
+    V *o = out + b0 * (M + 1);
+    const int per = M + 1;
+    for (int idx = threadIdx.x; idx < valid * per; idx += blockDim.x) {
+        const int l = idx / per;
+        const int k = idx - l * per;
+        const V zk = tile(l, k == M ? 0 : k);
+        const V zm = cconj(tile(l, k == 0 ? 0 : M - k));
+        const V e = cscale(cadd(zk, zm), T(0.5));
+        const V dd = csub(zk, zm);
+        const V od = cmk<V>(T(0.5) * dd.y, T(-0.5) * dd.x);  // (zk - zm) / (2i)
+        o[idx] = cadd(e, cmul(od, __ldg(post_tw + k)));
+    }
+}
+
+// Contiguous axis, M+1 bins -> real line of 2M points (backward, last stage):
+// C2RPre builds Z from the half spectrum, an inverse DFT_M gives z, and z[m]
+// is stored as the real pair (x[2m], x[2m+1]) times `scale`.
+template <class F, typename V>
+__global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
+    k_c2r(const V *__restrict__ in, typename RealOf<V>::T *out, const __grid_constant__ StageDesc d,
+          const V *__restrict__ tw, const V *__restrict__ post_tw, long long nlines, int lines,
+          typename RealOf<V>::T scale)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sm = reinterpret_cast<V *>(smem_raw);
+    const int M = F::generic ? d.n : F::plan::n;
+    const long long b0 = (long long)blockIdx.x * lines;
+    const int valid = (int)min((long long)lines, nlines - b0);
+    const C2RPre<V> src{in + b0 * (M + 1), post_tw, M, valid};
+    const GlobalLinesOut<V> dst{reinterpret_cast<V *>(out) + b0 * M, M, valid, scale};
+    const MapButterflyFast map{};
+    if constexpr (F::generic) {
+        run_generic<+1, false, false>(d, tw, sm, lines, 0, map, src, dst);
+    } else {
+        const SmemLines<V> tile{sm, M};
+        run_plan<typename F::plan, +1, false>(tw, lines, map, src, tile, dst);
+    }
+}
+
+// The six kernels of one family as untyped entry points for the host.
+template <class F, typename V> KernelSet kernel_set(int n, int npass, const int *radix)
+{
+    KernelSet k{};
+    k.n = n;
+    k.npass = npass;
+    for (int i = 0; i < npass && i < kMaxPasses; ++i) k.radix[i] = radix[i];
+    k.fn[KS_STRIDED_FWD] = (const void *)k_strided<F, -1, V>;
+    k.fn[KS_STRIDED_BWD] = (const void *)k_strided<F, +1, V>;
+    k.fn[KS_CONTIG_FWD] = (const void *)k_contig<F, -1, V>;
+    k.fn[KS_CONTIG_BWD] = (const void *)k_contig<F, +1, V>;
+    k.fn[KS_R2C] = (const void *)k_r2c<F, V>;
+    k.fn[KS_C2R] = (const void *)k_c2r<F, V>;
+    k.max_threads = F::template threads<V>();
+    k.generic = F::generic;
+    return k;
+}
+
+// Line lengths with specialised kernels and their radix sequences (n first,
+// then the radices in pass order).
+#define AFFT_LINE_PLANS(X)                                                                          \
+    X(1) X(2, 2) X(4, 4) X(8, 8) X(16, 16) X(24, 8, 3) X(32, 8, 4) X(48, 16, 3) X(60, 4, 3, 5)     \
+    X(64, 8, 8) X(80, 16, 5) X(96, 8, 4, 3) X(120, 8, 3, 5) X(128, 16, 8) X(160, 8, 4, 5)           \
+    X(192, 8, 8, 3) X(256, 16, 16) X(384, 16, 8, 3) X(512, 8, 8, 8) X(1024, 16, 8, 8)
+
+}  // namespace afft

@@ -1,0 +1,99 @@
+"""The C ABI without a GPU: the library builds, loads, exports every symbol the
+header declares, and rejects bad arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1506_07933_gb300 import afft
+from paper_1506_07933_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "afft.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return afft.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(afft_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("afft_plan_create", "afft_execute_forward", "afft_execute_backward", "afft_plan_destroy",
+              "afft_plan_workspace_bytes", "afft_status_string"):
+        assert s in syms
+    assert sorted(afft.EXPORTS) == syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+
+
+def _create(lib, n, kind, prec):
+    p = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * 3)(*n)
+    return lib.afft_plan_create(ctypes.byref(p), arr, kind, prec), p
+
+
+@pytest.mark.parametrize("n,kind,prec,code", [
+    ((8, 8, 7), 0, 0, 2),        # prime factor 7
+    ((0, 8, 8), 0, 0, 2),        # zero size
+    ((8, -4, 8), 0, 1, 2),       # negative size
+    ((8, 8, 11), 1, 0, 2),       # size check precedes the parity check
+    ((8, 8, 9), 1, 0, 3),        # r2c with odd n2
+    ((8, 8, 8), 5, 0, 4),        # kind
+    ((8, 8, 8), 0, 7, 5),        # precision
+    ((8, 8, 8), 0, 2, 9),        # split precision: not in this version
+    ((8, 8, 8192), 0, 0, 9),     # longer line than one CTA holds
+    ((8, 8, 16384), 1, 1, 9),    # r2c half length 8192
+])
+def test_plan_create_rejects_bad_arguments(lib, n, kind, prec, code):
+    st, p = _create(lib, n, kind, prec)
+    assert st == code, (st, afft.status_string(st))
+    assert not p.value
+
+
+def test_null_arguments(lib):
+    arr = (ctypes.c_int64 * 3)(8, 8, 8)
+    assert lib.afft_plan_create(None, arr, 0, 0) == 1
+    p = ctypes.c_void_p()
+    assert lib.afft_plan_create(ctypes.byref(p), None, 0, 0) == 1
+    assert lib.afft_plan_destroy(None) == 0
+    assert lib.afft_execute_forward(None, None, None, None) == 1
+    assert lib.afft_execute_backward(None, None, None, None) == 1
+    assert lib.afft_execute_forward_host(None, None, None, None, None, None) == 1
+    assert lib.afft_fill_uniform(None, 4, 1, 0, None) == 1
+    assert lib.afft_plan_workspace_bytes(None) == 0
+    assert lib.afft_plan_input_bytes(None) == 0
+    assert lib.afft_plan_launches(None, 0) == 0
+
+
+def test_status_strings(lib):
+    seen = set()
+    for code in range(10):
+        s = afft.status_string(code)
+        assert s and s != "unknown status"
+        seen.add(s)
+    assert len(seen) == 10
+    assert afft.status_string(99) == "unknown status"
+
+
+def test_error_is_raised_from_python(lib):
+    with pytest.raises(afft.AfftError) as e:
+        afft.afft_plan_create((8, 8, 7), afft.C2C, afft.F32)
+    assert e.value.status == 2
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(afft, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        afft.load(str(tmp_path / "libafft.so"))

@@ -1,0 +1,354 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
+
+Tolerances are relative L2 errors ||y - y_oracle|| / ||y_oracle||: 1e-12 for
+FP64 and 2e-6 for FP32.  FP32 results are compared with the oracle run in
+FP64 on the same FP32-rounded input, so the tolerance measures the kernels'
+rounding only.  Each error is printed (pytest -s shows them).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1506_07933_gb300 import afft, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-6}
+CDT = {"f64": np.complex128, "f32": np.complex64}
+RDT = {"f64": np.float64, "f32": np.float32}
+
+# every line length with specialised kernels, and some that take the generic ones
+SPEC_LENGTHS = [1, 2, 4, 8, 16, 24, 32, 48, 60, 64, 80, 96, 120, 128, 160, 192, 256, 384, 512, 1024]
+GENERIC_LENGTHS = [3, 5, 6, 9, 10, 12, 18, 25, 27, 36, 45, 50, 72, 81, 100, 125, 150, 243, 250, 320,
+                   640, 729, 768, 2048, 4096]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.set_device(0)
+    afft.load()
+    yield
+
+
+def report(name, err, tol):
+    print("\n[parity] %-48s rel_l2 = %.3e (tol %.0e)" % (name, err, tol))
+    assert err <= tol, (name, err, tol)
+
+
+def gpu_c2c(x, prec, direction=-1):
+    with afft.Plan(x.shape, "c2c", prec) as p:
+        t = torch.from_numpy(np.ascontiguousarray(x.astype(CDT[prec]))).cuda()
+        y = p.forward(t) if direction < 0 else p.backward(t)
+        torch.cuda.synchronize()
+        return y.cpu().numpy()
+
+
+def gpu_r2c(x, prec):
+    with afft.Plan(x.shape, "r2c", prec) as p:
+        y = p.forward(torch.from_numpy(np.ascontiguousarray(x.astype(RDT[prec]))).cuda())
+        torch.cuda.synchronize()
+        return y.cpu().numpy()
+
+
+def gpu_c2r(X, shape, prec):
+    with afft.Plan(shape, "r2c", prec) as p:
+        t = torch.from_numpy(np.ascontiguousarray(X.astype(CDT[prec]))).cuda()
+        before = t.clone()
+        y = p.backward(t)
+        torch.cuda.synchronize()
+        assert torch.equal(t, before), "c2r modified its input"
+        return y.cpu().numpy()
+
+
+# --- the small c2c configuration: 32^3 complex128 against the naive DFT ---------
+
+def test_c2c_32cubed_complex128_against_naive_dft():
+    x = synth.uniform_complex((32, 32, 32), 1506)
+    ref = oracle.c2c(x, -1, "naive")
+    X = gpu_c2c(x, "f64")
+    report("c2c 32^3 f64 forward vs naive", oracle.rel_l2(X, ref), 1e-12)
+    back = gpu_c2c(ref, "f64", +1)
+    report("c2c 32^3 f64 backward vs naive", oracle.rel_l2(back, oracle.c2c(ref, +1, "naive")), 1e-12)
+    report("c2c 32^3 f64 round trip", oracle.rel_l2(gpu_c2c(X, "f64", +1), x), 1e-12)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_c2c_32cubed_both_precisions(prec):
+    x = synth.uniform_complex((32, 32, 32), 1506).astype(CDT[prec])
+    report("c2c 32^3 %s forward" % prec, oracle.rel_l2(gpu_c2c(x, prec), oracle.c2c(x, -1, "naive")), TOL[prec])
+
+
+# --- every line length, on every axis --------------------------------------------
+
+@pytest.mark.parametrize("n", SPEC_LENGTHS + GENERIC_LENGTHS)
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_c2c_each_length_on_each_axis(n, prec):
+    other = (6, 10) if n <= 512 else (2, 3)
+    for shape in ((n,) + other, (other[0], n, other[1]), other + (n,)):
+        x = synth.uniform_complex(shape, n).astype(CDT[prec])
+        ref = oracle.c2c(x, -1, "fft")
+        report("c2c %s %s fwd" % (shape, prec), oracle.rel_l2(gpu_c2c(x, prec), ref), TOL[prec])
+        report("c2c %s %s bwd" % (shape, prec),
+               oracle.rel_l2(gpu_c2c(ref.astype(CDT[prec]), prec, +1),
+                             oracle.c2c(ref.astype(CDT[prec]), +1, "fft")), TOL[prec])
+
+
+@pytest.mark.parametrize("m", SPEC_LENGTHS + [3, 5, 12, 36, 100, 2048])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_r2c_c2r_each_half_length(m, prec):
+    shape = (6, 5, 2 * m) if m <= 512 else (2, 3, 2 * m)
+    x = synth.uniform_real(shape, m).astype(RDT[prec])
+    ref = oracle.r2c(x)
+    X = gpu_r2c(x, prec)
+    report("r2c %s %s" % (shape, prec), oracle.rel_l2(X, ref), TOL[prec])
+    Xr = ref.astype(CDT[prec])
+    report("c2r %s %s" % (shape, prec), oracle.rel_l2(gpu_c2r(Xr, shape, prec), oracle.c2r(Xr, shape[2])),
+           TOL[prec])
+
+
+# --- edge cases ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 8), (1, 8, 1), (8, 1, 1), (5, 1, 3), (1, 1, 2),
+                                   (2, 2, 2), (3, 1, 2), (16, 3, 1)])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_degenerate_shapes(shape, prec):
+    x = synth.uniform_complex(shape, 7).astype(CDT[prec])
+    report("c2c %s %s" % (shape, prec), oracle.rel_l2(gpu_c2c(x, prec), oracle.c2c(x, -1, "fft")), TOL[prec])
+    report("c2c bwd %s %s" % (shape, prec),
+           oracle.rel_l2(gpu_c2c(x, prec, +1), oracle.c2c(x, +1, "fft")), TOL[prec])
+    if shape[2] % 2 == 0:
+        r = x.real.copy()
+        report("r2c %s %s" % (shape, prec), oracle.rel_l2(gpu_r2c(r, prec), oracle.r2c(r)), TOL[prec])
+        H = oracle.r2c(r).astype(CDT[prec])
+        report("c2r %s %s" % (shape, prec), oracle.rel_l2(gpu_c2r(H, shape, prec), oracle.c2r(H, shape[2])),
+               TOL[prec])
+
+
+@pytest.mark.parametrize("shape", [(6, 10, 34), (5, 9, 514), (3, 40, 258), (32, 3, 66)])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_ragged_tiles(shape, prec):
+    """Column counts that do not fill the last tile (n2/2+1 odd, few lines per CTA)."""
+    x = synth.uniform_real(shape, 21).astype(RDT[prec])
+    ref = oracle.r2c(x)
+    report("r2c ragged %s %s" % (shape, prec), oracle.rel_l2(gpu_r2c(x, prec), ref), TOL[prec])
+    H = ref.astype(CDT[prec])
+    report("c2r ragged %s %s" % (shape, prec), oracle.rel_l2(gpu_c2r(H, shape, prec), oracle.c2r(H, shape[2])),
+           TOL[prec])
+
+
+def test_c2r_drops_imaginary_parts_of_self_conjugate_bins():
+    shape = (4, 6, 16)
+    H = oracle.r2c(synth.uniform_real(shape, 3))
+    G = H.copy()
+    G[:, :, 0] += 0.5j
+    G[:, :, 8] -= 0.25j
+    report("c2r non-Hermitian bins", oracle.rel_l2(gpu_c2r(G, shape, "f64"), oracle.c2r(G, 16)), 1e-12)
+
+
+# --- the r2c/c2r configuration: 256^3 and 512^3 random-mode fields -------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_r2c_c2r_256cubed_random_modes(prec):
+    shape = (256, 256, 256)
+    f = synth.random_mode_field(shape, 2561, n_modes=64, noise=1e-3)
+    x = f.astype(RDT[prec])
+    ref = oracle.r2c(x)
+    with afft.Plan(shape, "r2c", prec) as p:
+        X = p.forward(torch.from_numpy(x).cuda())
+        y = p.backward(X)
+        torch.cuda.synchronize()
+        Xh, yh = X.cpu().numpy(), y.cpu().numpy()
+    report("r2c 256^3 %s forward" % prec, oracle.rel_l2(Xh, ref), TOL[prec])
+    Hr = ref.astype(CDT[prec])
+    with afft.Plan(shape, "r2c", prec) as p:
+        yb = p.backward(torch.from_numpy(Hr).cuda())
+        torch.cuda.synchronize()
+    report("c2r 256^3 %s backward" % prec, oracle.rel_l2(yb.cpu().numpy(), oracle.c2r(Hr, 256)), TOL[prec])
+    report("r2c+c2r 256^3 %s round trip" % prec, oracle.rel_l2(yh, x), TOL[prec])
+
+
+def closed_form_half_spectrum(n, modes):
+    ks, amp, phase = modes
+    N = float(n) ** 3
+    H = {}
+    for k, a, ph in zip(ks, amp, phase):
+        for sgn in (1, -1):
+            kk = sgn * k
+            if kk[2] >= 0 and 2 * kk[2] <= n:
+                key = (int(kk[0] % n), int(kk[1] % n), int(kk[2]))
+                H[key] = H.get(key, 0) + N / 2 * a * np.exp(sgn * 1j * ph)
+    return H
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_r2c_512cubed_full_size(prec):
+    """512^3 in the benchmark's launch configuration.  Noise-free field: the whole
+    spectrum is known in closed form.  Noisy field: sampled bins from the DFT
+    definition, plus the round trip."""
+    n = 512
+    shape = (n, n, n)
+    f, modes = synth.random_mode_field(shape, 5121, n_modes=64, noise=0.0, return_modes=True)
+    H = closed_form_half_spectrum(n, modes)
+    x = torch.from_numpy(f.astype(RDT[prec])).cuda()
+    with afft.Plan(shape, "r2c", prec) as p:
+        X = p.forward(x)
+        torch.cuda.synchronize()
+        keys = list(H.keys())
+        idx = torch.tensor(keys, device="cuda").T
+        vals = torch.tensor([H[k] for k in keys], dtype=torch.complex128, device="cuda")
+        got = X[idx[0], idx[1], idx[2]].to(torch.complex128)
+        Xe = X.to(torch.complex128)
+        Xe[idx[0], idx[1], idx[2]] -= vals
+        err = float(torch.linalg.vector_norm(Xe) / torch.linalg.vector_norm(vals))
+        del Xe, got
+        # the noise-free input is rounded to FP32 for the f32 case: measure against the closed
+        # form of the rounded field only through the bound it must still meet
+        report("r2c 512^3 %s vs closed form" % prec, err, TOL[prec])
+        y = p.backward(X)
+        torch.cuda.synchronize()
+        rt = float(torch.linalg.vector_norm((y - x).to(torch.float64)) / torch.linalg.vector_norm(x.to(torch.float64)))
+        report("r2c+c2r 512^3 %s round trip" % prec, rt, TOL[prec])
+        del X, y
+    g = synth.random_mode_field(shape, 5121, n_modes=64, noise=1e-3).astype(RDT[prec])
+    rng = np.random.default_rng(512)
+    ks = np.stack([rng.integers(0, n, 6), rng.integers(0, n, 6), rng.integers(0, n // 2 + 1, 6)], 1)
+    ks = np.concatenate([ks, np.array(list(H.keys())[:6])])
+    ref = oracle.dft_bins(g, ks)
+    with afft.Plan(shape, "r2c", prec) as p:
+        G = p.forward(torch.from_numpy(g).cuda())
+        torch.cuda.synchronize()
+        got = G[ks[:, 0], ks[:, 1], ks[:, 2]].cpu().numpy()
+    report("r2c 512^3 %s sampled bins (%d)" % (prec, len(ks)), oracle.rel_l2(got, ref), TOL[prec])
+
+
+# --- the large c2c configuration: 1024^3 complex64 ------------------------------------
+
+def test_c2c_1024_subcase_256cubed_splitmix_input():
+    """The 1024^3 workload's error is stated on its 256^3 sub-case (same generator)."""
+    shape = (256, 256, 256)
+    x = synth.splitmix64_uniform(256 ** 3, 2560).reshape(shape)
+    t = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    afft.fill_uniform(t, 2560)
+    torch.cuda.synchronize()
+    assert np.array_equal(t.cpu().numpy(), x), "device generator differs from its CPU definition"
+    ref = oracle.c2c(x, -1, "fft")
+    with afft.Plan(shape, "c2c", "f32") as p:
+        X = p.forward(t)
+        torch.cuda.synchronize()
+    report("c2c 256^3 f32 (1024^3 sub-case)", oracle.rel_l2(X.cpu().numpy(), ref), TOL["f32"])
+
+
+def test_c2c_1024cubed_full_size_properties():
+    """1024^3 complex64 (8 GB): round trip and Parseval on the splitmix input, and a plane
+    wave that must come out as a single delta of height N."""
+    n = 1024
+    shape = (n, n, n)
+    N = float(n) ** 3
+    x = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    afft.fill_uniform(x, 10240)
+    with afft.Plan(shape, "c2c", "f32") as p:
+        X = p.forward(x)
+        torch.cuda.synchronize()
+        px = float(torch.sum(torch.abs(x.to(torch.complex128)) ** 2))
+        pX = float(torch.sum(torch.abs(X.to(torch.complex128)) ** 2))
+        report("c2c 1024^3 f32 Parseval", abs(pX / (N * px) - 1), TOL["f32"])
+        y = p.backward(X)
+        torch.cuda.synchronize()
+        rt = float(torch.linalg.vector_norm((y - x).to(torch.complex128)) / torch.linalg.vector_norm(x.to(torch.complex128)))
+        report("c2c 1024^3 f32 round trip", rt, TOL["f32"])
+        del X, y
+        k = (3, 1000, 17)
+        j = torch.arange(n, device="cuda", dtype=torch.float64)
+        e = [torch.exp(2j * np.pi * torch.remainder(j * kk, n) / n) for kk in k]
+        pw = (e[0][:, None, None] * e[1][None, :, None] * e[2][None, None, :]).to(torch.complex64)
+        x.copy_(pw)
+        del pw
+        X = p.forward(x)
+        torch.cuda.synchronize()
+        peak = complex(X[k].item())
+        X[k] = 0
+        rest = float(torch.linalg.vector_norm(X.to(torch.complex128)))
+        report("c2c 1024^3 f32 plane-wave peak", abs(peak - N) / N, TOL["f32"])
+        report("c2c 1024^3 f32 plane-wave leakage", rest / N, TOL["f32"])
+
+
+# --- the boundary's behaviour on a GPU ------------------------------------------------
+
+def test_in_place_and_overlap_are_rejected():
+    with afft.Plan((8, 8, 8), "c2c", "f32") as p:
+        t = torch.zeros((8, 8, 8), dtype=torch.complex64, device="cuda")
+        ptr = t.data_ptr()
+        with pytest.raises(afft.AfftError) as e:
+            afft.afft_execute_forward(p._p, ptr, ptr, 0)
+        assert e.value.status == 7
+        with pytest.raises(afft.AfftError) as e:
+            afft.afft_execute_forward(p._p, ptr, ptr + 8, 0)
+        assert e.value.status == 7
+
+
+def test_sizes_and_workspace():
+    with afft.Plan((16, 8, 32), "r2c", "f64") as p:
+        assert p.input_bytes == 16 * 8 * 32 * 8
+        assert p.output_bytes == 16 * 8 * 17 * 16
+        assert p.workspace_bytes == 16 * 8 * 17 * 16
+        assert p.launches(False) == 3 and p.launches(True) == 3
+    with afft.Plan((16, 8, 32), "c2c", "f32") as p:
+        assert p.workspace_bytes == 0
+
+
+def test_runs_on_a_side_stream():
+    shape = (32, 48, 64)
+    x = synth.uniform_complex(shape, 99).astype(np.complex64)
+    s = torch.cuda.Stream()
+    with afft.Plan(shape, "c2c", "f32") as p:
+        t = torch.from_numpy(x).cuda()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            X = p.forward(t)
+        s.synchronize()
+        report("c2c on a side stream", oracle.rel_l2(X.cpu().numpy(), oracle.c2c(x)), TOL["f32"])
+
+
+@pytest.mark.parametrize("kind,prec", [("c2c", "f32"), ("r2c", "f64")])
+def test_host_buffer_entry_points(kind, prec):
+    shape = (16, 20, 24)
+    with afft.Plan(shape, kind, prec) as p:
+        if kind == "c2c":
+            x = torch.from_numpy(synth.uniform_complex(shape, 5).astype(CDT[prec]))
+        else:
+            x = torch.from_numpy(synth.uniform_real(shape, 5).astype(RDT[prec]))
+        hin = x.pin_memory()
+        hout = torch.empty(p.spectral_shape, dtype=p.spectral_dtype).pin_memory()
+        din = torch.empty(p.spatial_shape, dtype=p.spatial_dtype, device="cuda")
+        dout = torch.empty(p.spectral_shape, dtype=p.spectral_dtype, device="cuda")
+        p.forward_host(hin, hout, din, dout)
+        torch.cuda.synchronize()
+        ref = p.forward(x.cuda()).cpu()
+        torch.cuda.synchronize()
+        assert torch.equal(hout, ref)
+        back = torch.empty(p.spatial_shape, dtype=p.spatial_dtype).pin_memory()
+        p.backward_host(hout, back, dout.clone(), din)
+        torch.cuda.synchronize()
+        report("host-buffer round trip %s %s" % (kind, prec), oracle.rel_l2(back.numpy(), x.numpy()), TOL[prec])
+
+
+def test_fill_uniform_matches_cpu_definition():
+    t = torch.empty(1000, dtype=torch.complex128, device="cuda")
+    afft.fill_uniform(t, 77)
+    torch.cuda.synchronize()
+    ref = synth.splitmix64_uniform(1000, 77).astype(np.complex128)
+    assert np.array_equal(t.cpu().numpy(), ref)
+
+
+def test_plans_are_independent():
+    a = afft.Plan((8, 12, 16), "c2c", "f32")
+    b = afft.Plan((8, 12, 16), "r2c", "f64")
+    x = synth.uniform_complex((8, 12, 16), 1).astype(np.complex64)
+    ya = a.forward(torch.from_numpy(x).cuda())
+    b.close()
+    ya2 = a.forward(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    assert torch.equal(ya, ya2)
+    a.close()
