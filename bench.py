@@ -1,0 +1,415 @@
+"""Benchmark of the 3-D FFT hot path on GB300: one JSON line on rank 0.
+
+Workload (one "step"): the r2c forward transform and the c2r backward
+transform of one 512^3 float32 random-mode field (64 Fourier modes with
+|k| <= n/4 plus 1e-3 Gaussian noise), i.e. every stage of the pencil
+algorithm in both directions.  Inputs are larger than L2 (537 MB vs 129 MB),
+so no explicit flush is needed between steps.
+
+value = whole-job algorithmic bytes per second as a percentage of one GB300's
+measured HBM bandwidth (MEASURED_PEAKS.json), the algorithmic bytes being
+the 3-pass minimum: one full-array read and write per axis stage.  At N GPUs
+every rank runs its own independent replica (the transform does not shard
+without an all-to-all), and the percentages add up (weak scaling).
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead (the
+only other place this script runs oracle code), on a bounded sample of the
+same workload, reported in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3-D FFT %HBM roofline at 512^3/1024^3 FP32/FP64; batched solves/s & p99"
+UNIT = "% of one GB300's measured HBM bandwidth (3-pass algorithmic bytes), summed over GPUs"
+FALLBACK_HBM_GBS = 6800.0
+SHAPE = (512, 512, 512)
+WORKLOAD = ("r2c forward + c2r backward, 512x512x512 %s random-mode field (64 modes, |k|<=n/4, "
+            "+1e-3 noise)")
+STAGE_NAMES_FWD = ["r2c z-stage (N2)", "strided y-stage (N1)", "strided x-stage (N0)"]
+STAGE_NAMES_BWD = ["strided x-stage (N0)", "strided y-stage (N1)", "c2r z-stage (N2)"]
+KERNEL_NAMES_FWD = ["k_r2c", "k_strided", "k_strided"]
+KERNEL_NAMES_BWD = ["k_strided", "k_strided", "k_c2r"]
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload_bytes(shape, real_bytes, cplx_bytes):
+    """3-pass algorithmic bytes of r2c forward (and, mirrored, c2r backward), per stage."""
+    n0, n1, n2 = shape
+    N = n0 * n1 * n2
+    Nh = n0 * n1 * (n2 // 2 + 1)
+    z = N * real_bytes + Nh * cplx_bytes
+    y = 2 * Nh * cplx_bytes
+    x = 2 * Nh * cplx_bytes
+    return z, y, x
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1506_07933_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on these sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = source_hash()
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("src") == src:
+            return int(kv["dram_bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU leg --
+
+def cpu_oracle_sample(min_seconds=10.0, shape=(128, 128, 128)):
+    """Times the FP64 oracle (r2c + c2r, all host cores) on a smaller cube of the same kind.
+
+    Returns (seconds per sample step, bytes per sample step, threads, description)."""
+    import numpy as np
+    import oracle
+    from paper_1506_07933_gb300 import synth
+
+    x = synth.random_mode_field(shape, 5121, n_modes=64, noise=1e-3)
+    threads = oracle.max_threads()
+    oracle.c2r(oracle.r2c(x), shape[2])  # warm up
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        X = oracle.r2c(x, "fft", threads)
+        oracle.c2r(X, shape[2], "fft", threads)
+        reps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    z, y, xx = workload_bytes(shape, 8, 16)
+    desc = ("oracle r2c+c2r (recursive mixed-radix, FP64) of a %dx%dx%d random-mode field, %d rep(s), "
+            "%d threads; extrapolated to the 512^3 step by algorithmic bytes" % (shape + (reps, threads)))
+    return dt, 2 * (z + y + xx), threads, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    peak, _ = peaks()
+    sample = (128, 128, 128)
+    times = []
+    per_step_bytes = None
+    for i in range(args.warmup + args.steps):
+        dt, b, threads, desc = cpu_oracle_sample(min_seconds=0.0, shape=sample)
+        per_step_bytes = b
+        if i >= args.warmup:
+            times.append(dt)
+    t = statistics.median(times)
+    value = 100.0 * per_step_bytes / t / 1e9 / peak
+    full_bytes = 2 * sum(workload_bytes(SHAPE, 4, 8))
+    t_full = t * full_bytes / per_step_bytes   # the 512^3 step at the sample's byte rate
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "sample_ms_per_step": t * 1e3,
+        "config": {"workload": WORKLOAD % "float32",
+                   "sample": "FP64 CPU oracle on a %dx%dx%d field of the same kind per step, scaled to the "
+                             "512^3 step by algorithmic bytes" % sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "r2c+c2r of a %dx%dx%d field per step" % sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg --
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1506_07933_gb300 import afft, synth
+    from paper_1506_07933_gb300 import build as libbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        dist.barrier()
+    afft.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    peak, peak_kind = peaks()
+    prec = args.precision
+    real_b, cplx_b = (4, 8) if prec == "f32" else (8, 16)
+    rdt = np.float32 if prec == "f32" else np.float64
+    plan = afft.Plan(SHAPE, "r2c", prec)
+    field = synth.random_mode_field(SHAPE, 5121 + rank, n_modes=64, noise=1e-3).astype(rdt)
+    x = torch.from_numpy(field).cuda()
+    X = torch.empty(plan.spectral_shape, dtype=plan.spectral_dtype, device="cuda")
+    y = torch.empty(plan.spatial_shape, dtype=plan.spatial_dtype, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.forward(x, X)
+        plan.backward(X, y)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    plan.timing_begin(2 * args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    stage = plan.timing_end()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    z, yb, xb = workload_bytes(SHAPE, real_b, cplx_b)
+    step_bytes = 2 * (z + yb + xb)
+    value = 100.0 * world * step_bytes / (ms * 1e-3) / 1e9 / peak
+
+    # dominant kernel from the per-stage events of the timed region
+    fwd = [r for i, r in enumerate(stage) if i % 2 == 0]
+    bwd = [r for i, r in enumerate(stage) if i % 2 == 1]
+    kernels = []
+    for rows, names, knames, sbytes in ((fwd, STAGE_NAMES_FWD, KERNEL_NAMES_FWD, (z, yb, xb)),
+                                        (bwd, STAGE_NAMES_BWD, KERNEL_NAMES_BWD, (xb, yb, z))):
+        for s in range(3):
+            ts = [r[s] for r in rows]
+            kernels.append({"stage": names[s] + (" fwd" if rows is fwd else " bwd"), "kernel": knames[s],
+                            "mean_ms": sum(ts) / len(ts), "bytes": sbytes[s],
+                            "gbs": sbytes[s] / (sum(ts) / len(ts) * 1e-3) / 1e9})
+    total_stage_ms = sum(k["mean_ms"] for k in kernels)
+    dom = max(kernels, key=lambda k: k["mean_ms"])
+    workload_tag = "512c_r2c_%s" % prec
+    traffic = profiled_traffic(dom["stage"].replace(" ", "_"), workload_tag)
+    roofline = {"bound": "hbm", "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": dom["gbs"] / peak, "traffic": traffic, "kernel": dom["kernel"],
+                "stage": dom["stage"], "peak_source": peak_kind,
+                "bytes_per_launch": dom["bytes"], "mean_launch_ms": dom["mean_ms"]}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, plan, field, x, X, y, stream, barrier, world, step_bytes, peak, torch, dist)
+    launches = args.steps * (plan.launches(False) + plan.launches(True))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": WORKLOAD % {"f32": "float32", "f64": "float64"}[prec],
+                   "l2": "inputs larger than L2 (%d MB > 129 MB), no flush" % (plan.input_bytes >> 20),
+                   "bytes_per_step": step_bytes, "parallelism": "replicas x%d" % world},
+        "roofline": roofline,
+        "stages": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in kk.items()} for kk in kernels],
+        "stage_ms_total": total_stage_ms,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    del x, X, y
+    plan.close()
+    torch.cuda.empty_cache()
+
+    if args.extra and rank == 0:
+        line["also"] = extra_configs(afft, torch, peak)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        dt, b, threads, desc = cpu_oracle_sample(min_seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": 100.0 * b / dt / 1e9 / peak, "unit": UNIT, "cores": threads,
+                                "kind": "oracle", "sample": desc,
+                                "ms_per_step_extrapolated": dt * 1e3 * step_bytes / b}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def measure_e2e(args, plan, field, x, X, y, stream, barrier, world, step_bytes, peak, torch, dist):
+    """The step end to end through the host-buffer C-ABI entry points (pinned host memory)."""
+    hx = torch.from_numpy(field).pin_memory()
+    hX = torch.empty(plan.spectral_shape, dtype=plan.spectral_dtype).pin_memory()
+    hy = torch.empty(plan.spatial_shape, dtype=plan.spatial_dtype).pin_memory()
+    dspec = torch.empty_like(X)
+
+    def e2e_step():
+        plan.forward_host(hx, hX, x, X)
+        plan.backward_host(hX, hy, dspec, y)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = plan.input_bytes + plan.output_bytes
+    d2h = plan.output_bytes + plan.input_bytes
+    return {"value": 100.0 * world * step_bytes / (e2e_ms * 1e-3) / 1e9 / peak, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+            "call": "afft_execute_forward_host + afft_execute_backward_host"}
+
+
+def extra_configs(afft, torch, peak):
+    """The other roofline configurations of the metric, fewer repetitions, same method."""
+    out = []
+    for shape, kind, prec in (((512,) * 3, "r2c", "f64"), ((512,) * 3, "c2c", "f32"),
+                              ((512,) * 3, "c2c", "f64"), ((1024,) * 3, "c2c", "f32")):
+        p = afft.Plan(shape, kind, prec)
+        x = torch.empty(p.spatial_shape, dtype=p.spatial_dtype, device="cuda")
+        if kind == "c2c":
+            afft.fill_uniform(x, 10240)
+        else:
+            x.uniform_(-1, 1)
+        X = torch.empty(p.spectral_shape, dtype=p.spectral_dtype, device="cuda")
+        y = torch.empty(p.spatial_shape, dtype=p.spatial_dtype, device="cuda")
+        cb = 16 if prec == "f64" else 8
+        rb = cb // 2
+        if kind == "c2c":
+            N = shape[0] * shape[1] * shape[2]
+            b = 3 * 2 * N * cb
+        else:
+            b = sum(workload_bytes(shape, rb, cb))
+        for _ in range(3):
+            p.forward(x, X)
+            p.backward(X, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            p.forward(x, X)
+            p.backward(X, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out.append({"workload": "%s %dx%dx%d %s fwd+bwd" % ((kind,) + shape + (prec,)), "ms_per_step": ms,
+                    "frac_of_hbm_roofline": 2 * b / (ms * 1e-3) / 1e9 / peak})
+        del x, X, y
+        p.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["afft", "reference"], default="afft")
+    ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--extra", action="store_true", help="also time the other roofline configurations")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -140,6 +140,26 @@ size_t afft_plan_output_bytes(const afft_plan *p);
 /* Number of kernel launches one execute_forward / execute_backward makes. */
 int afft_plan_launches(const afft_plan *p, int backward);
 
+/*
+ * Per-stage timing (the tracing facility; not part of the transform).
+ * afft_plan_timing_begin makes the next `capacity` executions of this plan
+ * (forward or backward, device or host variant) record a CUDA event before
+ * the first stage and after each stage, on the execution's stream.  Events
+ * are host-side objects created here; execute still allocates no memory.
+ * Returns AFFT_ERR_SIZE for capacity < 1, AFFT_ERR_CUDA if event creation
+ * fails.  Calling it again discards earlier records.
+ */
+int afft_plan_timing_begin(afft_plan *p, int capacity);
+
+/*
+ * Waits for the recorded events, writes the elapsed milliseconds of each
+ * stage to ms[3 * r + s] (record r in execution order; stage s in launch
+ * order: forward N2, N1, N0 -- backward N0, N1, N2; a stage skipped for a
+ * length-1 axis reads 0), stores the number of records in *count (at most
+ * the capacity), and stops recording.  ms must hold 3 * capacity floats.
+ */
+int afft_plan_timing_end(afft_plan *p, float *ms, int *count);
+
 /* Static description of a status code. */
 const char *afft_status_string(int status);
 

@@ -38,6 +38,7 @@ EXPORTS = [
     "afft_execute_forward_host", "afft_execute_backward_host", "afft_plan_destroy",
     "afft_plan_workspace_bytes", "afft_plan_input_bytes", "afft_plan_output_bytes",
     "afft_plan_launches", "afft_status_string", "afft_fill_uniform",
+    "afft_plan_timing_begin", "afft_plan_timing_end",
 ]
 
 _lib = None
@@ -72,9 +73,12 @@ def load(path: str = None):
     lib.afft_status_string.argtypes = [c_int]
     lib.afft_status_string.restype = ctypes.c_char_p
     lib.afft_fill_uniform.argtypes = [vp, ctypes.c_int64, ctypes.c_uint64, c_int, vp]
+    lib.afft_plan_timing_begin.argtypes = [vp, c_int]
+    lib.afft_plan_timing_end.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(c_int)]
     for f in ("afft_plan_create", "afft_execute_forward", "afft_execute_backward",
               "afft_execute_forward_host", "afft_execute_backward_host", "afft_plan_destroy",
-              "afft_plan_launches", "afft_fill_uniform"):
+              "afft_plan_launches", "afft_fill_uniform", "afft_plan_timing_begin",
+              "afft_plan_timing_end"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -228,6 +232,19 @@ class Plan:
                 raise ValueError("%s must be a contiguous CPU tensor %s %s" % (w, dt, shape))
         afft_execute_backward_host(self._p, host_in.data_ptr(), host_out.data_ptr(), dev_in.data_ptr(),
                                    dev_out.data_ptr(), _stream_handle(stream))
+
+    def timing_begin(self, capacity: int) -> None:
+        """Record per-stage CUDA events for the next ``capacity`` executions."""
+        _check(load().afft_plan_timing_begin(self._p, int(capacity)), "afft_plan_timing_begin")
+        self._timing_cap = int(capacity)
+
+    def timing_end(self):
+        """Per-stage milliseconds, one row of 3 per recorded execution (launch order)."""
+        cap = getattr(self, "_timing_cap", 0)
+        buf = (ctypes.c_float * (3 * max(cap, 1)))()
+        cnt = ctypes.c_int(0)
+        _check(load().afft_plan_timing_end(self._p, buf, ctypes.byref(cnt)), "afft_plan_timing_end")
+        return [list(buf[3 * r:3 * r + 3]) for r in range(cnt.value)]
 
     def close(self):
         if getattr(self, "_p", None):

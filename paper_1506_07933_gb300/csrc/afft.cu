@@ -35,6 +35,10 @@ struct afft_plan {
     void *d_work;          // c2r workspace: n0*n1*nh complex
     size_t work_bytes;
     int device;
+    // per-stage timing (afft_plan_timing_begin / _end)
+    std::vector<cudaEvent_t> events;   // 4 per record
+    int timing_cap;
+    int timing_count;
 };
 
 namespace {
@@ -325,6 +329,13 @@ cudaError_t c2r(const AxisPlan &a, const V *in, T *out, const V *tw, const V *po
     return launch(a, KS_C2R, args, s);
 }
 
+// Records the timing event `i` (0..3) of the current record, if timing is on.
+void mark(afft_plan *p, int i, cudaStream_t s)
+{
+    if (p->timing_count < p->timing_cap) cudaEventRecord(p->events[4 * p->timing_count + i], s);
+    if (i == 3 && p->timing_count < p->timing_cap) ++p->timing_count;
+}
+
 template <typename V>
 int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
@@ -333,11 +344,15 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
     const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh;
     V *o = (V *)out;
     cudaError_t e;
+    mark(p, 0, s);
     if (p->kind == AFFT_C2C) e = contig<V>(p->ax[2], (const V *)in, o, tw, n0 * n1, 0, 1.0, s);
     else e = r2c<V, T>(p->ax[2], (const T *)in, o, tw, tw + p->post_off, n0 * n1, s);
     if (e != cudaSuccess) return AFFT_ERR_CUDA;
+    mark(p, 1, s);
     if (n1 > 1 && (e = strided<V>(p->ax[1], o, o, tw, nh, 0, s)) != cudaSuccess) return AFFT_ERR_CUDA;
+    mark(p, 2, s);
     if (n0 > 1 && (e = strided<V>(p->ax[0], o, o, tw, n1 * nh, 0, s)) != cudaSuccess) return AFFT_ERR_CUDA;
+    mark(p, 3, s);
     return AFFT_OK;
 }
 
@@ -350,12 +365,17 @@ int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
     const double scale = 1.0 / ((double)p->n[0] * (double)p->n[1] * (double)p->n[2]);
     // C2C works in `out`; c2r works in the plan's workspace and writes real `out` last.
     V *buf = p->kind == AFFT_C2C ? (V *)out : (V *)p->d_work;
+    mark(p, 0, s);
     cudaError_t e = strided<V>(p->ax[0], (const V *)in, buf, tw, n1 * nh, 1, s);
     if (e != cudaSuccess) return AFFT_ERR_CUDA;
+    mark(p, 1, s);
     if (n1 > 1 && (e = strided<V>(p->ax[1], buf, buf, tw, nh, 1, s)) != cudaSuccess) return AFFT_ERR_CUDA;
+    mark(p, 2, s);
     if (p->kind == AFFT_C2C) e = contig<V>(p->ax[2], buf, (V *)out, tw, n0 * n1, 1, scale, s);
     else e = c2r<V, T>(p->ax[2], buf, (T *)out, tw, tw + p->post_off, n0 * n1, scale, s);
-    return e == cudaSuccess ? AFFT_OK : AFFT_ERR_CUDA;
+    if (e != cudaSuccess) return AFFT_ERR_CUDA;
+    mark(p, 3, s);
+    return AFFT_OK;
 }
 
 size_t in_bytes(const afft_plan *p)
@@ -422,9 +442,8 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
     const int64_t zlen = kind == AFFT_R2C ? n[2] / 2 : n[2];
     if (n[0] > kMaxLine || n[1] > kMaxLine || zlen > kMaxLine) return AFFT_ERR_UNSUPPORTED;
 
-    afft_plan *p = new (std::nothrow) afft_plan;
+    afft_plan *p = new (std::nothrow) afft_plan();
     if (!p) return AFFT_ERR_NOMEM;
-    std::memset(p, 0, sizeof *p);
     for (int i = 0; i < 3; ++i) p->n[i] = n[i];
     p->kind = kind;
     p->precision = precision;
@@ -525,8 +544,50 @@ int afft_plan_destroy(afft_plan *p)
         if (p->d_tw) cudaFree(p->d_tw);
         if (p->d_work) cudaFree(p->d_work);
     }
+    for (cudaEvent_t ev : p->events) cudaEventDestroy(ev);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
+    return st;
+}
+
+int afft_plan_timing_begin(afft_plan *p, int capacity)
+{
+    if (!p) return AFFT_ERR_NULL;
+    if (capacity < 1) return AFFT_ERR_SIZE;
+    for (cudaEvent_t ev : p->events) cudaEventDestroy(ev);
+    p->events.clear();
+    p->timing_cap = 0;
+    p->timing_count = 0;
+    p->events.resize((size_t)capacity * 4);
+    for (size_t i = 0; i < p->events.size(); ++i) {
+        if (cudaEventCreate(&p->events[i]) != cudaSuccess) {
+            for (size_t j = 0; j < i; ++j) cudaEventDestroy(p->events[j]);
+            p->events.clear();
+            return AFFT_ERR_CUDA;
+        }
+    }
+    p->timing_cap = capacity;
+    return AFFT_OK;
+}
+
+int afft_plan_timing_end(afft_plan *p, float *ms, int *count)
+{
+    if (!p || !ms || !count) return AFFT_ERR_NULL;
+    const int n = p->timing_count;
+    int st = AFFT_OK;
+    if (n > 0 && cudaEventSynchronize(p->events[4 * n - 1]) != cudaSuccess) st = AFFT_ERR_CUDA;
+    for (int r = 0; r < n && st == AFFT_OK; ++r)
+        for (int k = 0; k < 3; ++k) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p->events[4 * r + k], p->events[4 * r + k + 1]) != cudaSuccess) {
+                st = AFFT_ERR_CUDA;
+                break;
+            }
+            ms[3 * r + k] = t;
+        }
+    *count = n;
+    p->timing_cap = 0;  // stop recording; the events are kept for the next begin
+    p->timing_count = 0;
     return st;
 }
 
