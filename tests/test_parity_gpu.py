@@ -199,7 +199,7 @@ def test_r2c_512cubed_full_size(prec):
         idx = torch.tensor(keys, device="cuda").T
         vals = torch.tensor([H[k] for k in keys], dtype=torch.complex128, device="cuda")
         got = X[idx[0], idx[1], idx[2]].to(torch.complex128)
-        Xe = X.to(torch.complex128)
+        Xe = X.to(torch.complex128, copy=True)   # never an alias of X (X is complex128 for f64)
         Xe[idx[0], idx[1], idx[2]] -= vals
         err = float(torch.linalg.vector_norm(Xe) / torch.linalg.vector_norm(vals))
         del Xe, got
