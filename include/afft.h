@@ -76,7 +76,8 @@ enum {
     AFFT_ERR_NOMEM = 6,       /* device or host allocation failed in create    */
     AFFT_ERR_INPLACE = 7,     /* in == out                                     */
     AFFT_ERR_CUDA = 8,        /* a CUDA call or kernel launch failed           */
-    AFFT_ERR_UNSUPPORTED = 9  /* valid request this version does not implement */
+    AFFT_ERR_UNSUPPORTED = 9, /* valid request this version does not implement */
+    AFFT_ERR_SCRATCH = 10     /* afft_c2r_noalloc: the transform does not fit its fixed scratch */
 };
 
 /*
@@ -174,6 +175,39 @@ const char *afft_status_string(int status);
  */
 int afft_fill_uniform(void *dev_out, int64_t count, uint64_t seed, int precision,
                       void *cuda_stream);
+
+/*
+ * Size of the fixed device array used by afft_c2r_noalloc: 64 MiB, held on
+ * every GPU that loads this library until the process exits.  The first
+ * 512 KiB hold twiddle tables, the rest the intermediate spectrum.
+ */
+#define AFFT_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/*
+ * Backward transform of an r2c plan (c2r: complex [n0][n1][n2/2+1] -> real
+ * [n0][n1][n2], x 1/N) that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- a host
+ * framework that owns all device memory through its own arena and refuses
+ * (or cannot account for) foreign allocations, or a latency-bound loop that
+ * must not stall on the allocator once running -- and therefore cannot create
+ * a plan.  Its twiddle tables and intermediate live in one file-scope
+ * __device__ array of AFFT_NOALLOC_SCRATCH_BYTES; the caller passes `in`
+ * (device, not modified) and `out` (device), laid out as for
+ * afft_execute_backward on an AFFT_R2C plan of the same n and precision, and
+ * gets the same result.
+ *   n:         host array of 3 sizes (n[2] even), as afft_plan_create.
+ *   precision: AFFT_F32 or AFFT_F64.
+ *   stream:    a cudaStream_t (NULL = legacy default stream); asynchronous.
+ * Errors as afft_plan_create / afft_execute_backward, plus AFFT_ERR_SCRATCH when
+ * n0*n1*(n2/2+1) complex values exceed the array's 63.5 MiB workspace part
+ * (e.g. 256^3 float32 does not fit; 128^3 float64 does).
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it: make that first call before any
+ * stream capture.  All calls share the array and leave their data in it:
+ * calls whose work overlaps on the GPU (other streams or host threads) race
+ * and corrupt each other's results; calls on one stream are safe.
+ */
+int afft_c2r_noalloc(const int64_t n[3], int precision, const void *in, void *out, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,7 @@ PRECISIONS = {"f32": F32, "f64": F64, "f32_split": F32_SPLIT}
 STATUS = {
     0: "AFFT_OK", 1: "AFFT_ERR_NULL", 2: "AFFT_ERR_SIZE", 3: "AFFT_ERR_R2C_ODD", 4: "AFFT_ERR_KIND",
     5: "AFFT_ERR_PRECISION", 6: "AFFT_ERR_NOMEM", 7: "AFFT_ERR_INPLACE", 8: "AFFT_ERR_CUDA",
-    9: "AFFT_ERR_UNSUPPORTED",
+    9: "AFFT_ERR_UNSUPPORTED", 10: "AFFT_ERR_SCRATCH",
 }
 
 # Every symbol include/afft.h declares.
@@ -38,7 +38,7 @@ EXPORTS = [
     "afft_execute_forward_host", "afft_execute_backward_host", "afft_plan_destroy",
     "afft_plan_workspace_bytes", "afft_plan_input_bytes", "afft_plan_output_bytes",
     "afft_plan_launches", "afft_status_string", "afft_fill_uniform",
-    "afft_plan_timing_begin", "afft_plan_timing_end",
+    "afft_plan_timing_begin", "afft_plan_timing_end", "afft_c2r_noalloc",
 ]
 
 _lib = None
@@ -75,10 +75,11 @@ def load(path: str = None):
     lib.afft_fill_uniform.argtypes = [vp, ctypes.c_int64, ctypes.c_uint64, c_int, vp]
     lib.afft_plan_timing_begin.argtypes = [vp, c_int]
     lib.afft_plan_timing_end.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(c_int)]
+    lib.afft_c2r_noalloc.argtypes = [i64p, c_int, vp, vp, vp]
     for f in ("afft_plan_create", "afft_execute_forward", "afft_execute_backward",
               "afft_execute_forward_host", "afft_execute_backward_host", "afft_plan_destroy",
               "afft_plan_launches", "afft_fill_uniform", "afft_plan_timing_begin",
-              "afft_plan_timing_end"):
+              "afft_plan_timing_end", "afft_c2r_noalloc"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -133,6 +134,12 @@ def afft_plan_destroy(plan) -> None:
 def afft_fill_uniform(ptr: int, count: int, seed: int, precision: int, stream: int) -> None:
     _check(load().afft_fill_uniform(ptr, int(count), int(seed), int(precision), stream),
            "afft_fill_uniform")
+
+
+def afft_c2r_noalloc(shape, precision: int, in_ptr: int, out_ptr: int, stream: int) -> None:
+    """c2r backward without any allocation (fixed 64 MiB device array); see include/afft.h."""
+    n = (ctypes.c_int64 * 3)(*[int(s) for s in shape])
+    _check(load().afft_c2r_noalloc(n, int(precision), in_ptr, out_ptr, stream), "afft_c2r_noalloc")
 
 
 # --------------------------------------------------------------- tensor API --

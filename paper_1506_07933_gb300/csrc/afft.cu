@@ -423,6 +423,7 @@ const char *afft_status_string(int status)
     case AFFT_ERR_INPLACE: return "in-place or overlapping buffers are not supported";
     case AFFT_ERR_CUDA: return "CUDA error";
     case AFFT_ERR_UNSUPPORTED: return "not supported by this version";
+    case AFFT_ERR_SCRATCH: return "transform exceeds the fixed no-allocation scratch array";
     default: return "unknown status";
     }
 }
