@@ -77,7 +77,8 @@ enum {
     AFFT_ERR_INPLACE = 7,     /* in == out                                     */
     AFFT_ERR_CUDA = 8,        /* a CUDA call or kernel launch failed           */
     AFFT_ERR_UNSUPPORTED = 9, /* valid request this version does not implement */
-    AFFT_ERR_SCRATCH = 10     /* afft_c2r_noalloc: the transform does not fit its fixed scratch */
+    AFFT_ERR_SCRATCH = 10,    /* afft_c2r_noalloc: the transform does not fit its fixed scratch */
+    AFFT_ERR_TIMEOUT = 11     /* a kernel gave up a bounded wait (see afft_plan_device_status) */
 };
 
 /*
@@ -129,6 +130,15 @@ int afft_execute_backward_host(afft_plan *p, const void *host_in, void *host_out
 /* Destroy a plan and free its device memory.  NULL is a no-op (AFFT_OK).
  * Synchronises the plan's device before freeing. */
 int afft_plan_destroy(afft_plan *p);
+
+/*
+ * Failure detection.  Kernels that wait for asynchronous tile copies bound the
+ * wait (about 2 s); a CTA that gives up records it in a flag the plan owns and
+ * returns early, leaving that tile's output unwritten.  This call
+ * synchronises with the device, returns AFFT_ERR_TIMEOUT if any execution since
+ * the last call recorded such a timeout (and clears the flag), else AFFT_OK.
+ */
+int afft_plan_device_status(afft_plan *p);
 
 /* Bytes of device workspace the plan holds (0 for a NULL plan). */
 size_t afft_plan_workspace_bytes(const afft_plan *p);

@@ -29,7 +29,7 @@ PRECISIONS = {"f32": F32, "f64": F64, "f32_split": F32_SPLIT}
 STATUS = {
     0: "AFFT_OK", 1: "AFFT_ERR_NULL", 2: "AFFT_ERR_SIZE", 3: "AFFT_ERR_R2C_ODD", 4: "AFFT_ERR_KIND",
     5: "AFFT_ERR_PRECISION", 6: "AFFT_ERR_NOMEM", 7: "AFFT_ERR_INPLACE", 8: "AFFT_ERR_CUDA",
-    9: "AFFT_ERR_UNSUPPORTED", 10: "AFFT_ERR_SCRATCH",
+    9: "AFFT_ERR_UNSUPPORTED", 10: "AFFT_ERR_SCRATCH", 11: "AFFT_ERR_TIMEOUT",
 }
 
 # Every symbol include/afft.h declares.
@@ -39,6 +39,7 @@ EXPORTS = [
     "afft_plan_workspace_bytes", "afft_plan_input_bytes", "afft_plan_output_bytes",
     "afft_plan_launches", "afft_status_string", "afft_fill_uniform",
     "afft_plan_timing_begin", "afft_plan_timing_end", "afft_c2r_noalloc",
+    "afft_plan_device_status",
 ]
 
 _lib = None
@@ -76,10 +77,11 @@ def load(path: str = None):
     lib.afft_plan_timing_begin.argtypes = [vp, c_int]
     lib.afft_plan_timing_end.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(c_int)]
     lib.afft_c2r_noalloc.argtypes = [i64p, c_int, vp, vp, vp]
+    lib.afft_plan_device_status.argtypes = [vp]
     for f in ("afft_plan_create", "afft_execute_forward", "afft_execute_backward",
               "afft_execute_forward_host", "afft_execute_backward_host", "afft_plan_destroy",
               "afft_plan_launches", "afft_fill_uniform", "afft_plan_timing_begin",
-              "afft_plan_timing_end", "afft_c2r_noalloc"):
+              "afft_plan_timing_end", "afft_c2r_noalloc", "afft_plan_device_status"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -239,6 +241,10 @@ class Plan:
                 raise ValueError("%s must be a contiguous CPU tensor %s %s" % (w, dt, shape))
         afft_execute_backward_host(self._p, host_in.data_ptr(), host_out.data_ptr(), dev_in.data_ptr(),
                                    dev_out.data_ptr(), _stream_handle(stream))
+
+    def device_status(self) -> int:
+        """Synchronises; returns 0, or 11 (AFFT_ERR_TIMEOUT) if a bounded wait ran out since the last call."""
+        return int(load().afft_plan_device_status(self._p))
 
     def timing_begin(self, capacity: int) -> None:
         """Record per-stage CUDA events for the next ``capacity`` executions."""

@@ -12,6 +12,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/afft.h"
 #include "afft_internal.h"
 
@@ -22,6 +24,9 @@ struct AxisPlan {
     Launch launch;
     const KernelSet *ks;   // kernels for this line length (specialised or generic)
     int tw_base;           // first twiddle of this axis in the plan's table; desc.tw_off is relative
+    // pipelined strided kernel (persistent CTAs) when the family has one
+    bool pipe;
+    int pipe_slots;        // CTAs resident at once (SMs x CTAs per SM): the persistent grid's cap
 };
 
 struct afft_plan {
@@ -29,16 +34,20 @@ struct afft_plan {
     int kind;
     int precision;
     int64_t nh;            // last-axis length of the complex array: n2 (C2C) or n2/2+1 (R2C)
+    int64_t nhp;           // row pitch of the internal R2C layout: nh, or nh + 1 so that rows
+                           // are 16-byte aligned for TMA (then the workspace holds the N2, N1
+                           // stages and the N0 stage converts to/from the compact layout)
     AxisPlan ax[3];        // ax[2] transforms the contiguous axis (length n2, or n2/2 for R2C)
     int post_off;          // R2C: offset of the w_{n2}^k table (n2/2+1 entries)
     void *d_tw;            // twiddle tables (float2 or double2)
-    void *d_work;          // c2r workspace: n0*n1*nh complex
+    void *d_work;          // R2C workspace: n0*n1*nhp complex
     size_t work_bytes;
     int device;
     // per-stage timing (afft_plan_timing_begin / _end)
     std::vector<cudaEvent_t> events;   // 4 per record
     int timing_cap;
     int timing_count;
+    unsigned *d_err;       // set by a kernel whose bounded wait ran out
 };
 
 namespace {
@@ -251,7 +260,33 @@ int plan_shapes(afft_plan *p)
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
     if (max_smem <= 0) max_smem = 48 * 1024;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh;
+    // strided stages: persistent double-buffered kernels where the family has them
+    for (int a = 0; a < 2; ++a) {
+        AxisPlan &ap = p->ax[a];
+        ap.pipe = false;
+        const KernelSet *ks = ap.ks;
+        if (ks->generic || !ks->pipe[PIPE_FWD_TMA] || ks->pipe_smem > max_smem) continue;
+        for (int k = 0; k < PIPE_COUNT; ++k)
+            if (cudaFuncSetAttribute(ks->pipe[k], cudaFuncAttributeMaxDynamicSharedMemorySize, ks->pipe_smem) !=
+                cudaSuccess)
+                return AFFT_ERR_CUDA;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks->pipe[PIPE_FWD_TMA], ks->pipe_threads,
+                                                          ks->pipe_smem) != cudaSuccess || per_sm < 1)
+            continue;
+        ap.pipe_slots = sms * per_sm;
+        ap.pipe = true;
+    }
+    // FP32 r2c with an odd half-spectrum width: rows of nh complex64 are not 16-byte aligned,
+    // which TMA needs; keep the N2 and N1 stages in a workspace with rows of nh + 1 and let the
+    // (pipelined) N0 stage convert between that and the compact layout.
+    p->nhp = nh;
+    if (p->kind == AFFT_R2C && elem == 8 && (nh % 2) == 1 && n0 > 1 && p->ax[0].pipe) p->nhp = nh + 1;
+    p->ax[2].desc.ld = p->nhp != nh ? (int)p->nhp : 0;
+    const long long nhp = p->nhp;
     // Specialised kernels run two CTAs per SM: keep their tiles to half the SM.
     auto budget = [&](const AxisPlan &a) -> size_t {
         return a.ks->generic ? (size_t)max_smem : (size_t)std::min(max_smem, 112 * 1024);
@@ -259,7 +294,7 @@ int plan_shapes(afft_plan *p)
     AxisPlan &z = p->ax[2], &y = p->ax[1], &x = p->ax[0];
     if (!shape_contig(z.desc, n0 * n1, elem, z.ks->max_threads, budget(z), z.launch))
         return AFFT_ERR_UNSUPPORTED;
-    if (!shape_strided(y.desc, n0, nh, elem, y.ks->max_threads, budget(y), y.launch))
+    if (!shape_strided(y.desc, n0, nhp, elem, y.ks->max_threads, budget(y), y.launch))
         return AFFT_ERR_UNSUPPORTED;
     if (!shape_strided(x.desc, 1, n1 * nh, elem, x.ks->max_threads, budget(x), x.launch))
         return AFFT_ERR_UNSUPPORTED;
@@ -280,10 +315,76 @@ cudaError_t launch(const AxisPlan &a, int which, void **args, cudaStream_t s)
     return cudaLaunchKernel(a.ks->fn[which], dim3((unsigned)L.blocks), dim3(L.threads), args, L.smem, s);
 }
 
-template <typename V>
-cudaError_t strided(const AxisPlan &a, const V *in, V *out, const V *tw, long long W, int backward,
-                    cudaStream_t s)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
 {
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return (EncodeTiledFn)f;
+    }();
+    return fn;
+}
+
+// TMA view of a [outer][n][W] complex array as 8-byte elements: dims
+// (W * C/8, n, outer), box (lines * C/8, min(n, 256), 1).
+bool encode_strided_map(CUtensorMap *map, const void *base, long long outer, int n, long long W, size_t C,
+                        int lines)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const size_t per = C / 8;
+    if ((W * C) % 16 != 0 || ((uintptr_t)base) % 16 != 0 || W < lines) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)(W * per), (cuuint64_t)n, (cuuint64_t)outer};
+    cuuint64_t strides[2] = {(cuuint64_t)(W * C), (cuuint64_t)(n * W * C)};
+    cuuint32_t box[3] = {(cuuint32_t)(lines * per), (cuuint32_t)tma_box_rows(n), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Column remap of a strided stage (see afft_internal.h): remap_in == 0 keeps columns.
+struct Remap {
+    long long Wout;
+    int in, out;
+};
+
+template <typename V>
+cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, long long outer, long long W,
+                         int backward, unsigned *err, const Remap &rm, cudaStream_t s)
+{
+    alignas(64) CUtensorMap map;
+    std::memset(&map, 0, sizeof map);
+    const bool tma = encode_strided_map(&map, in, outer, a.desc.n, W, sizeof(V), a.ks->pipe_lines);
+    const int which = backward ? (tma ? PIPE_BWD_TMA : PIPE_BWD_CPASYNC) : (tma ? PIPE_FWD_TMA : PIPE_FWD_CPASYNC);
+    tw += a.tw_base;
+    long long tpo = (W + a.ks->pipe_lines - 1) / a.ks->pipe_lines;
+    long long nt = outer * tpo;
+    long long wout = rm.in > 0 ? rm.Wout : W;
+    int rin = rm.in, rout = rm.out;
+    const unsigned grid = (unsigned)std::min<long long>(nt, a.pipe_slots);
+    void *args[] = {(void *)&in, (void *)&out, (void *)&map, (void *)&tw, (void *)&W, (void *)&tpo, (void *)&nt,
+                    (void *)&err, (void *)&wout, (void *)&rin, (void *)&rout};
+    return cudaLaunchKernel(a.ks->pipe[which], dim3(grid), dim3(a.ks->pipe_threads), args,
+                            (size_t)a.ks->pipe_smem, s);
+}
+
+// A strided stage over a [outer][n][W] array (in place when in == out).  The
+// column remap needs the pipelined kernel; plans only ask for it then.
+template <typename V>
+cudaError_t strided(const AxisPlan &a, const V *in, V *out, const V *tw, long long outer, long long W,
+                    int backward, cudaStream_t s, unsigned *err, const Remap &rm = Remap{0, 0, 0})
+{
+    if (a.pipe) return strided_pipe<V>(a, in, out, tw, outer, W, backward, err, rm, s);
+    if (rm.in > 0) return cudaErrorInvalidValue;
     StageDesc d = a.desc;
     tw += a.tw_base;
     long long tpo = a.launch.tiles_per_outer;
@@ -341,17 +442,24 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
-    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh;
+    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh, nhp = p->nhp;
+    // padded R2C: N2 and N1 stages in the workspace, N0 stage converts to the compact `out`
     V *o = (V *)out;
+    V *w = nhp != nh ? (V *)p->d_work : o;
     cudaError_t e;
     mark(p, 0, s);
     if (p->kind == AFFT_C2C) e = contig<V>(p->ax[2], (const V *)in, o, tw, n0 * n1, 0, 1.0, s);
-    else e = r2c<V, T>(p->ax[2], (const T *)in, o, tw, tw + p->post_off, n0 * n1, s);
+    else e = r2c<V, T>(p->ax[2], (const T *)in, w, tw, tw + p->post_off, n0 * n1, s);
     if (e != cudaSuccess) return AFFT_ERR_CUDA;
     mark(p, 1, s);
-    if (n1 > 1 && (e = strided<V>(p->ax[1], o, o, tw, nh, 0, s)) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n1 > 1 && (e = strided<V>(p->ax[1], w, w, tw, n0, nhp, 0, s, p->d_err)) != cudaSuccess)
+        return AFFT_ERR_CUDA;
     mark(p, 2, s);
-    if (n0 > 1 && (e = strided<V>(p->ax[0], o, o, tw, n1 * nh, 0, s)) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n0 > 1) {
+        const Remap rm = nhp != nh ? Remap{n1 * nh, (int)nhp, (int)nh} : Remap{0, 0, 0};
+        if ((e = strided<V>(p->ax[0], w, o, tw, 1, n1 * nhp, 0, s, p->d_err, rm)) != cudaSuccess)
+            return AFFT_ERR_CUDA;
+    }
     mark(p, 3, s);
     return AFFT_OK;
 }
@@ -361,15 +469,17 @@ int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
-    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh;
+    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh, nhp = p->nhp;
     const double scale = 1.0 / ((double)p->n[0] * (double)p->n[1] * (double)p->n[2]);
     // C2C works in `out`; c2r works in the plan's workspace and writes real `out` last.
     V *buf = p->kind == AFFT_C2C ? (V *)out : (V *)p->d_work;
     mark(p, 0, s);
-    cudaError_t e = strided<V>(p->ax[0], (const V *)in, buf, tw, n1 * nh, 1, s);
+    const Remap rm = nhp != nh ? Remap{n1 * nhp, (int)nh, (int)nhp} : Remap{0, 0, 0};
+    cudaError_t e = strided<V>(p->ax[0], (const V *)in, buf, tw, 1, n1 * nh, 1, s, p->d_err, rm);
     if (e != cudaSuccess) return AFFT_ERR_CUDA;
     mark(p, 1, s);
-    if (n1 > 1 && (e = strided<V>(p->ax[1], buf, buf, tw, nh, 1, s)) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n1 > 1 && (e = strided<V>(p->ax[1], buf, buf, tw, n0, nhp, 1, s, p->d_err)) != cudaSuccess)
+        return AFFT_ERR_CUDA;
     mark(p, 2, s);
     if (p->kind == AFFT_C2C) e = contig<V>(p->ax[2], buf, (V *)out, tw, n0 * n1, 1, scale, s);
     else e = c2r<V, T>(p->ax[2], buf, (T *)out, tw, tw + p->post_off, n0 * n1, scale, s);
@@ -424,6 +534,7 @@ const char *afft_status_string(int status)
     case AFFT_ERR_CUDA: return "CUDA error";
     case AFFT_ERR_UNSUPPORTED: return "not supported by this version";
     case AFFT_ERR_SCRATCH: return "transform exceeds the fixed no-allocation scratch array";
+    case AFFT_ERR_TIMEOUT: return "a kernel's bounded wait ran out (asynchronous copy never completed)";
     default: return "unknown status";
     }
 }
@@ -472,8 +583,16 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
     int st = precision == AFFT_F64 ? plan_shapes<double2>(p) : plan_shapes<float2>(p);
     if (st == AFFT_OK)
         st = precision == AFFT_F64 ? upload_twiddles<double2>(p, tm, tl) : upload_twiddles<float2>(p, tm, tl);
+    if (st == AFFT_OK) {
+        if (cudaMalloc(&p->d_err, sizeof(unsigned)) != cudaSuccess) {
+            p->d_err = nullptr;
+            st = AFFT_ERR_NOMEM;
+        } else if (cudaMemset(p->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
+            st = AFFT_ERR_CUDA;
+        }
+    }
     if (st == AFFT_OK && kind == AFFT_R2C) {
-        p->work_bytes = (size_t)n[0] * n[1] * p->nh * cplx_size(precision);
+        p->work_bytes = (size_t)n[0] * n[1] * p->nhp * cplx_size(precision);
         if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) {
             p->d_work = nullptr;
             p->work_bytes = 0;
@@ -540,10 +659,11 @@ int afft_plan_destroy(afft_plan *p)
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     int st = AFFT_OK;
-    if (p->d_tw || p->d_work) {
+    if (p->d_tw || p->d_work || p->d_err) {
         if (cudaDeviceSynchronize() != cudaSuccess) st = AFFT_ERR_CUDA;
         if (p->d_tw) cudaFree(p->d_tw);
         if (p->d_work) cudaFree(p->d_work);
+        if (p->d_err) cudaFree(p->d_err);
     }
     for (cudaEvent_t ev : p->events) cudaEventDestroy(ev);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
@@ -590,6 +710,17 @@ int afft_plan_timing_end(afft_plan *p, float *ms, int *count)
     p->timing_cap = 0;  // stop recording; the events are kept for the next begin
     p->timing_count = 0;
     return st;
+}
+
+int afft_plan_device_status(afft_plan *p)
+{
+    if (!p) return AFFT_ERR_NULL;
+    if (!p->d_err) return AFFT_OK;
+    unsigned flag = 0;
+    if (cudaMemcpy(&flag, p->d_err, sizeof flag, cudaMemcpyDeviceToHost) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (flag == 0) return AFFT_OK;
+    cudaMemset(p->d_err, 0, sizeof(unsigned));
+    return AFFT_ERR_TIMEOUT;
 }
 
 size_t afft_plan_workspace_bytes(const afft_plan *p) { return p ? p->work_bytes : 0; }

@@ -25,6 +25,8 @@ struct StageDesc {
     int radix[kMaxPasses];         // radix of each pass
     int ns[kMaxPasses];            // product of the radices of the earlier passes
     int tw_off[kMaxPasses];        // first twiddle of each pass (complex entries)
+    int ld;                        // r2c/c2r stage: stride between half-spectrum lines, in complex
+                                   // elements; 0 means compact (M + 1 for a line of M points)
 };
 
 // Butterflies a thread carries per pass for radix R: at most 16 complex
@@ -33,6 +35,16 @@ struct StageDesc {
 __host__ __device__ constexpr int bmax_for_radix(int r)
 {
     return r >= 16 ? 1 : (r == 3 ? 5 : (r == 5 ? 3 : 16 / r));
+}
+
+// Rows per TMA box when a line of n rows is loaded in boxes of at most 256
+// rows: the largest divisor of n not above 256, so the boxes tile the line
+// exactly (used identically by the kernels and by the host's tensor maps).
+__host__ __device__ constexpr int tma_box_rows(int n)
+{
+    int r = n < 256 ? n : 256;
+    while (r > 1 && n % r != 0) --r;
+    return r;
 }
 
 struct Launch {
@@ -57,6 +69,16 @@ struct Launch {
 //             long long nlines, int lines, T scale)
 enum { KS_STRIDED_FWD = 0, KS_STRIDED_BWD, KS_CONTIG_FWD, KS_CONTIG_BWD, KS_R2C, KS_C2R, KS_COUNT };
 
+// Pipelined strided kernels (persistent CTAs, double-buffered tiles), indexed
+// by PIPE_*.  Signature: (const V *in, V *out, CUtensorMap map, const V *tw,
+// long long W, long long tiles_per_outer, long long ntiles, unsigned *err,
+// long long Wout, int remap_in, int remap_out); the TMA variants read through
+// `map`, the cp.async ones through `in`.  Input column c is stored to output
+// column c (remap_in == 0), or, with q = c / remap_in and k = c % remap_in,
+// to q * remap_out + k when k < remap_out and nowhere otherwise (used to move
+// between the compact and the padded half-spectrum layouts).
+enum { PIPE_FWD_TMA = 0, PIPE_FWD_CPASYNC, PIPE_BWD_TMA, PIPE_BWD_CPASYNC, PIPE_COUNT };
+
 struct KernelSet {
     int n;                         // line length (0 for the generic family)
     int npass;
@@ -64,6 +86,10 @@ struct KernelSet {
     const void *fn[KS_COUNT];
     int max_threads;               // largest CTA the kernels were compiled for
     bool generic;
+    const void *pipe[PIPE_COUNT];  // null when the family has no pipelined strided kernel
+    int pipe_lines;                // columns per tile of the pipelined kernel
+    int pipe_threads;              // its (compile-time) CTA size
+    int pipe_smem;                 // its dynamic shared memory (two tile buffers)
 };
 
 // Specialised kernels for line length n, or nullptr.

@@ -56,6 +56,20 @@ template <typename V> struct GlobalColsOut {
     }
 };
 
+// Output side of a strided tile whose columns are remapped between layouts:
+// every call comes from the thread that owns one column (line-fast maps with a
+// CTA size that is a multiple of the tile width), so the destination column
+// `col` (or -1 for "not stored") is resolved once per tile per thread.
+template <typename V> struct GlobalColRemapOut {
+    V *base;                       // &y[o][0][0]
+    long long W;                   // output row pitch
+    long long col;                 // this thread's output column, -1 to drop
+    __device__ __forceinline__ void operator()(int, int p, V v) const
+    {
+        if (col >= 0) base[(long long)p * W + col] = v;
+    }
+};
+
 // Global contiguous lines b0 .. b0+lines-1 of length n (contiguous stage).
 template <typename V> struct GlobalLines {
     const V *base;                 // &x[b0][0]
@@ -83,14 +97,15 @@ template <typename V> struct GlobalLinesOut {
 // with the imaginary parts of the self-conjugate bins X[0], X[M] dropped.
 // (The factor 1/2 of the textbook identity is folded into the 1/N scale.)
 template <typename V> struct C2RPre {
-    const V *base;                 // &X[b0][0], line stride M + 1
+    const V *base;                 // &X[b0][0]
     const V *post_tw;              // w_{2M}^k forward, k = 0..M
     int M;
+    int ld;                        // line stride (M + 1 compact, more when padded)
     int valid;
     __device__ __forceinline__ V operator()(int l, int k) const
     {
         if (l >= valid) return czero<V>();
-        const V *x = base + l * (M + 1);
+        const V *x = base + l * ld;
         V a = x[k];
         V b = cconj(x[M - k]);
         if (k == 0) {

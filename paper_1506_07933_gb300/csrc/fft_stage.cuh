@@ -55,18 +55,19 @@ struct MapButterflyFast {  // contiguous stage: consecutive threads walk along a
 // InPlace the pass reads everything into registers, waits for the whole CTA,
 // then writes.
 
-template <int R, int S, bool InPlace, typename V, class Map, class Src, class Dst>
+template <int R, int S, bool InPlace, int NT = 0, typename V, class Map, class Src, class Dst>
 __device__ __forceinline__ void radix_pass(int n, int Ns, const V *__restrict__ tw, int lines,
                                            const Map &map, const Src &src, const Dst &dst)
 {
     constexpr int B = bmax_for_radix(R);
+    const int nthr = NT > 0 ? NT : (int)blockDim.x;  // NT: compile-time CTA size, when known
     const int nb = n / R;
     const int total = lines * nb;
     V v[B][R];
     int lb[B], jb[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        const int idx = threadIdx.x + b * blockDim.x;
+        const int idx = threadIdx.x + b * nthr;
         lb[b] = -1;
         jb[b] = 0;
         if (idx < total) {
@@ -303,7 +304,8 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     if constexpr (F::generic) run_generic<-1, false, true>(d, tw, sm, lines, 0, map, src, tile);
     else run_plan<typename F::plan, -1, true>(tw, lines, map, src, tile, tile);
     __syncthreads();
-    V *o = out + b0 * (M + 1);
+    const int ld = d.ld > 0 ? d.ld : M + 1;  // output line stride (padded layouts leave a gap)
+    V *o = out + b0 * ld;
     const int per = M + 1;
     for (int idx = threadIdx.x; idx < valid * per; idx += blockDim.x) {
         const int l = idx / per;
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
         const V e = cscale(cadd(zk, zm), T(0.5));
         const V dd = csub(zk, zm);
         const V od = cmk<V>(T(0.5) * dd.y, T(-0.5) * dd.x);  // (zk - zm) / (2i)
-        o[idx] = cadd(e, cmul(od, __ldg(post_tw + k)));
+        o[l * ld + k] = cadd(e, cmul(od, __ldg(post_tw + k)));
     }
 }
 
@@ -331,7 +333,8 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     const int M = F::generic ? d.n : F::plan::n;
     const long long b0 = (long long)blockIdx.x * lines;
     const int valid = (int)min((long long)lines, nlines - b0);
-    const C2RPre<V> src{in + b0 * (M + 1), post_tw, M, valid};
+    const int ld = d.ld > 0 ? d.ld : M + 1;  // input line stride
+    const C2RPre<V> src{in + b0 * ld, post_tw, M, ld, valid};
     const GlobalLinesOut<V> dst{reinterpret_cast<V *>(out) + b0 * M, M, valid, scale};
     const MapButterflyFast map{};
     if constexpr (F::generic) {
@@ -340,24 +343,6 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
         const SmemLines<V> tile{sm, M};
         run_plan<typename F::plan, +1, false>(tw, lines, map, src, tile, dst);
     }
-}
-
-// The six kernels of one family as untyped entry points for the host.
-template <class F, typename V> KernelSet kernel_set(int n, int npass, const int *radix)
-{
-    KernelSet k{};
-    k.n = n;
-    k.npass = npass;
-    for (int i = 0; i < npass && i < kMaxPasses; ++i) k.radix[i] = radix[i];
-    k.fn[KS_STRIDED_FWD] = (const void *)k_strided<F, -1, V>;
-    k.fn[KS_STRIDED_BWD] = (const void *)k_strided<F, +1, V>;
-    k.fn[KS_CONTIG_FWD] = (const void *)k_contig<F, -1, V>;
-    k.fn[KS_CONTIG_BWD] = (const void *)k_contig<F, +1, V>;
-    k.fn[KS_R2C] = (const void *)k_r2c<F, V>;
-    k.fn[KS_C2R] = (const void *)k_c2r<F, V>;
-    k.max_threads = F::template threads<V>();
-    k.generic = F::generic;
-    return k;
 }
 
 // Line lengths with specialised kernels and their radix sequences (n first,

@@ -1,7 +1,7 @@
 // kernels_f64.cu -- instantiates the stage kernels for double2: one specialised
 // family per line length of AFFT_LINE_PLANS, plus the generic family.  (One
 // translation unit per precision, so the two compile in parallel.)
-#include "fft_stage.cuh"
+#include "fft_pipe.cuh"
 
 namespace afft {
 

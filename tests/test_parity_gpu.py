@@ -138,6 +138,18 @@ def test_ragged_tiles(shape, prec):
            TOL[prec])
 
 
+@pytest.mark.parametrize("shape", [(16, 24, 40), (64, 48, 96), (32, 3, 96), (120, 8, 12), (8, 1, 24)])
+def test_r2c_padded_internal_layout(shape):
+    """FP32 r2c plans whose half-spectrum width n2/2+1 is odd keep the N2/N1 stages in a
+    workspace with an even row pitch and convert in the N0 stage; results must not change."""
+    x = synth.uniform_real(shape, 31).astype(np.float32)
+    ref = oracle.r2c(x)
+    report("r2c padded %s f32" % (shape,), oracle.rel_l2(gpu_r2c(x, "f32"), ref), TOL["f32"])
+    H = ref.astype(np.complex64)
+    report("c2r padded %s f32" % (shape,), oracle.rel_l2(gpu_c2r(H, shape, "f32"), oracle.c2r(H, shape[2])),
+           TOL["f32"])
+
+
 def test_c2r_drops_imaginary_parts_of_self_conjugate_bins():
     shape = (4, 6, 16)
     H = oracle.r2c(synth.uniform_real(shape, 3))
