@@ -124,55 +124,150 @@ template <int LG> struct MapLineFastC {
     }
 };
 
-// All passes with the tile already in shared memory: every pass but the
-// last runs in place there; the last one writes to dst.
-template <int S, int NT, bool First, int N, int Ns, int TwOff, typename V, class Map, class Sm, class Dst, int R,
-          int... Rest>
-__device__ __forceinline__ void run_passes_smem(Seq<R, Rest...>, const V *tw, int lines, const Map &map,
-                                                const Sm &sm, const Dst &dst)
-{
-    constexpr bool Last = sizeof...(Rest) == 0;
-    if (!First) __syncthreads();
-    if constexpr (Last) radix_pass<R, S, false, NT>(N, Ns, tw + TwOff, lines, map, sm, dst);
-    else radix_pass<R, S, true, NT>(N, Ns, tw + TwOff, lines, map, sm, sm);
-    if constexpr (!Last) {
-        constexpr int next = TwOff + (Ns > 1 ? Ns * (R - 1) : 0);
-        run_passes_smem<S, NT, false, N, Ns * R, next>(Seq<Rest...>{}, tw, lines, map, sm, dst);
-    }
-}
-
+// ------------------------------------------------------------------ shape ---
 // Compile-time shape of the pipelined strided kernel for line length N and
-// complex type V: 128-byte rows, halved while two tile buffers exceed
-// kPipeSmemCap; threads so that each carries at most 16 values per pass.
-constexpr int kPipeSmemCap = 144 * 1024;
+// complex type V.  A tile is LINES columns x N rows with 128-byte rows
+// (LINES = 16 for complex64, 8 for complex128), halved while three tile
+// buffers (two load targets and one scratch for out-of-place passes) exceed
+// kPipeSmemCap.  FP32 passes of radix <= 8 give each thread two adjacent
+// columns ("pairs": 16-byte shared-memory and global accesses, one twiddle
+// load for both); other passes give each thread one column.  Every thread
+// carries at most 16 complex values per pass.
+constexpr int kPipeSmemCap = 200 * 1024;
 
 template <class P, typename V> struct PipeShape {
     static constexpr int row_lines = 128 / (int)sizeof(V);
-    static constexpr int lines_for(int l)
+    __host__ __device__ static constexpr int lines_for(int l)
     {
-        return (l > 1 && 2 * P::n * l * (int)sizeof(V) > kPipeSmemCap) ? lines_for(l / 2) : l;
+        return (l > 1 && 3 * P::n * l * (int)sizeof(V) > kPipeSmemCap) ? lines_for(l / 2) : l;
     }
     static constexpr int lines = lines_for(row_lines);
     static constexpr int lg = lines == 16 ? 4 : lines == 8 ? 3 : lines == 4 ? 2 : lines == 2 ? 1 : 0;
-    template <int... Rs> static constexpr int threads_for(Seq<Rs...>)
+    __host__ __device__ static constexpr bool pairs(int r) { return sizeof(V) == 8 && lines >= 2 && 2 * r <= 16; }
+    __host__ __device__ static constexpr int per_thread(int r)   // butterflies (or butterfly pairs) per thread
+    {
+        return pairs(r) ? (16 / (2 * r) > 0 ? 16 / (2 * r) : 1) : bmax_for_radix(r);
+    }
+    __host__ __device__ static constexpr int units(int r) { return (pairs(r) ? lines / 2 : lines) * (P::n / r); }
+    template <int... Rs> __host__ __device__ static constexpr int threads_for(Seq<Rs...>)
     {
         int req = lines;
         for (int r : {Rs...}) {
-            const int bf = lines * (P::n / r);
-            const int per = bmax_for_radix(r);
-            const int t = (bf + per - 1) / per;
+            const int t = (units(r) + per_thread(r) - 1) / per_thread(r);
             req = t > req ? t : req;
         }
         return (req + 31) / 32 * 32;
     }
     static constexpr int threads = threads_for(typename P::seq{});
-    static_assert(threads % lines == 0, "each thread must own one column of the tile");
-    static constexpr int tile = P::n * lines;                  // complex elements per tile
-    static constexpr int smem = 2 * tile * (int)sizeof(V) + 16; // two buffers, then two mbarriers
+    static_assert(threads % lines == 0, "each thread must own fixed columns of the tile");
+    static constexpr int tile = P::n * lines;                       // complex elements per tile
+    static constexpr int smem = 3 * tile * (int)sizeof(V) + 16;     // 3 buffers, then two mbarriers
     static constexpr int box_rows = tma_box_rows(P::n);
     static_assert((box_rows * lines * (int)sizeof(V)) % 128 == 0 || box_rows == P::n,
                   "TMA boxes must start 128-byte aligned in shared memory");
 };
+
+// ---------------------------------------------------------- pair passes ---
+
+// Writes of a pair pass: shared memory rows, or the stage's global output.
+template <int LG> struct PairSmemOut {
+    float2 *sm;
+    __device__ __forceinline__ void operator()(int lp, int p, float2 lo, float2 hi) const
+    {
+        reinterpret_cast<float4 *>(sm)[(p << (LG - 1)) + lp] = make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+};
+struct PairGlobalOut {
+    float2 *base;                  // &y[o][0][0]
+    long long W;                   // output row pitch
+    long long oc0, oc1;            // this thread's two output columns (-1: not stored)
+    bool vec;                      // adjacent, 16-byte aligned: one 16-byte store
+    __device__ __forceinline__ void operator()(int, int p, float2 lo, float2 hi) const
+    {
+        float2 *row = base + (long long)p * W;
+        if (vec) {
+            *reinterpret_cast<float4 *>(row + oc0) = make_float4(lo.x, lo.y, hi.x, hi.y);
+        } else {
+            if (oc0 >= 0) row[oc0] = lo;
+            if (oc1 >= 0) row[oc1] = hi;
+        }
+    }
+};
+
+// One radix-R Stockham pass over a [N][2^LG] float2 tile, out of place; the
+// thread's butterflies are (column pair lp, butterfly j), reading both
+// columns' R values with 16-byte loads and sharing the twiddles.
+template <int R, int S, int N, int Ns, int LG, int NT, int B, class Dst>
+__device__ __forceinline__ void pair_pass(const float2 *src, const float2 *__restrict__ tw, const Dst &dst)
+{
+    constexpr int PAIRS = (1 << LG) / 2, NB = N / R, TOTAL = PAIRS * NB;
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int idx = threadIdx.x + b * NT;
+        if (B * NT == TOTAL || idx < TOTAL) {
+            const int lp = idx % PAIRS, j = idx / PAIRS;
+            float2 lo[R], hi[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float4 q = s4[(j + r * NB) * PAIRS + lp];
+                lo[r] = make_float2(q.x, q.y);
+                hi[r] = make_float2(q.z, q.w);
+            }
+            const int k = j % Ns;
+            if (Ns > 1) {
+                const float2 *t = tw + k * (R - 1);
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float2 w = __ldg(t + r - 1);
+                    lo[r] = ctw<S>(lo[r], w);
+                    hi[r] = ctw<S>(hi[r], w);
+                }
+            }
+            Dft<R, S, float2>::run(lo);
+            Dft<R, S, float2>::run(hi);
+            const int o = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst(lp, o + r * Ns, lo[r], hi[r]);
+        }
+    }
+}
+
+// The stage's global output for both pass kinds, resolved per thread per tile.
+template <typename V> struct TileOut {
+    GlobalColRemapOut<V> single;   // one column per thread
+    PairGlobalOut pair;            // two columns per thread (float2 only)
+};
+
+// Passes Seq<R, Rest...>: pass number Q reads buffer X (Q even) or C (Q odd)
+// and writes the other one; the last pass writes the stage's output.
+template <class Sh, int S, int N, int Ns, int TwOff, int Q, typename V, int R, int... Rest>
+__device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V *tw, const TileOut<V> &out)
+{
+    constexpr bool Last = sizeof...(Rest) == 0;
+    constexpr int LG = Sh::lg, NT = Sh::threads;
+    V *src = (Q % 2 == 0) ? X : C;
+    V *dst = (Q % 2 == 0) ? C : X;
+    if constexpr (Sh::pairs(R)) {
+        constexpr int B = Sh::per_thread(R);
+        if constexpr (Last) pair_pass<R, S, N, Ns, LG, NT, B>(src, tw + TwOff, out.pair);
+        else pair_pass<R, S, N, Ns, LG, NT, B>(src, tw + TwOff, PairSmemOut<LG>{dst});
+    } else {
+        const SmemRowsC<V, LG> in_rows{src};
+        if constexpr (Last)
+            radix_pass<R, S, false, NT>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows, out.single);
+        else
+            radix_pass<R, S, false, NT>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                        SmemRowsC<V, LG>{dst});
+    }
+    if constexpr (!Last) {
+        __syncthreads();
+        constexpr int next = TwOff + (Ns > 1 ? Ns * (R - 1) : 0);
+        pipe_passes<Sh, S, N, Ns * R, next, Q + 1>(Seq<Rest...>{}, X, C, tw, out);
+    }
+}
+
+// ---------------------------------------------------------------- kernel ---
 
 template <class P, int S, typename V, bool TMA>
 __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
@@ -184,8 +279,9 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
     constexpr unsigned TILE_BYTES = TILE * sizeof(V);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    V *const buf0 = reinterpret_cast<V *>(smem_raw);  // buffer b starts at buf0 + b * TILE
-    unsigned long long *const bars = reinterpret_cast<unsigned long long *>(smem_raw + 2 * TILE_BYTES);
+    V *const buf0 = reinterpret_cast<V *>(smem_raw);   // load buffer b at buf0 + b * TILE
+    V *const scratch = buf0 + 2 * TILE;                  // out-of-place passes
+    unsigned long long *const bars = reinterpret_cast<unsigned long long *>(smem_raw + 3 * TILE_BYTES);
     const int tid = threadIdx.x;
 
     long long t = blockIdx.x;
@@ -223,40 +319,44 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
             cp_async_commit();
         }
     };
+    auto out_col = [&](long long c) -> long long {
+        if (c >= W) return -1;
+        if (remap_in <= 0) return c;
+        const long long q = c / remap_in, k = c - q * remap_in;
+        return k < remap_out ? q * remap_out + k : -1;
+    };
 
     issue(t, 0);
     for (int i = 0;; ++i) {
         const int b = i & 1;
-        const long long tn = t + gridDim.x;
-        const bool more = tn < ntiles;
-        if (more) issue(tn, b ^ 1);
+        // wait for this tile; the barrier also retires every read of the other buffer
         if constexpr (TMA) {
             const bool ok = mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1));
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) atomicExch(err, 1u);
-                // let copies still in flight land before the CTA's shared memory goes away
-                if (more) mbar_wait_bounded(&bars[b ^ 1], (unsigned)(((i + 1) >> 1) & 1));
                 return;
             }
         } else {
-            if (more) cp_async_wait<1>();
-            else cp_async_wait<0>();
+            cp_async_wait<0>();
             __syncthreads();
         }
+        const long long tn = t + gridDim.x;
+        if (tn < ntiles) issue(tn, b ^ 1);   // next tile flies while this one is transformed
+
         const long long o = t / tiles_per_outer;
         const long long c0 = (t - o * tiles_per_outer) * LINES;
-        // this thread's column (every pass maps it to the same column: NT is a multiple of LINES)
-        const long long c = c0 + (tid & (LINES - 1));
-        long long oc = c < W ? c : -1;
-        if (remap_in > 0 && oc >= 0) {
-            const long long q = c / remap_in, k = c - q * remap_in;
-            oc = k < remap_out ? q * remap_out + k : -1;
+        TileOut<V> to;
+        to.single = GlobalColRemapOut<V>{out + o * (long long)N * Wout, Wout, out_col(c0 + (tid & (LINES - 1)))};
+        if constexpr (sizeof(V) == 8) {
+            const int lp = tid % (LINES / 2 > 0 ? LINES / 2 : 1);
+            const long long a = out_col(c0 + 2 * lp), bcol = out_col(c0 + 2 * lp + 1);
+            float2 *base = reinterpret_cast<float2 *>(out + o * (long long)N * Wout);
+            const bool vec = a >= 0 && bcol == a + 1 && (a % 2) == 0 && (Wout % 2) == 0 &&
+                             (reinterpret_cast<unsigned long long>(base) & 15) == 0;
+            to.pair = PairGlobalOut{base, Wout, a, bcol, vec};
         }
-        const GlobalColRemapOut<V> dst{out + o * (long long)N * Wout, Wout, oc};
-        const SmemRowsC<V, LG> tile{buf0 + b * TILE};
-        run_passes_smem<S, NT, true, N, 1, 0>(typename P::seq{}, tw, LINES, MapLineFastC<LG>{}, tile, dst);
-        __syncthreads();
-        if (!more) break;
+        pipe_passes<Sh, S, N, 1, 0, 0>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to);
+        if (tn >= ntiles) break;
         t = tn;
     }
 }
