@@ -148,6 +148,22 @@ size_t afft_plan_workspace_bytes(const afft_plan *p);
 size_t afft_plan_input_bytes(const afft_plan *p);
 size_t afft_plan_output_bytes(const afft_plan *p);
 
+/*
+ * L2-resident stage fusion.  The N2 and N1 stages can run slab by slab (a slab
+ * is a range of N0 planes): the N2 stage of slab c, then the N1 stage of slab c
+ * on a second stream the plan owns, while the N2 stage of slab c+1 runs, so the
+ * N1 stage reads its slab from L2 instead of HBM (AccFFT's stage order, Algorithm
+ * 1, is unchanged; only the schedule is).  `bytes` is the slab size to aim for;
+ * 0 runs the stages unfused (the default).  Plans whose array is under three
+ * slabs are not fused.  Creates the
+ * second stream and its events (no device memory).  Execute still returns
+ * asynchronously and joins the second stream back into the caller's stream.
+ */
+int afft_plan_set_l2_chunk(afft_plan *p, size_t bytes);
+
+/* Slab size in use (0 when the stages run unfused). */
+size_t afft_plan_l2_chunk(const afft_plan *p);
+
 /* Number of kernel launches one execute_forward / execute_backward makes. */
 int afft_plan_launches(const afft_plan *p, int backward);
 
@@ -166,7 +182,9 @@ int afft_plan_timing_begin(afft_plan *p, int capacity);
  * Waits for the recorded events, writes the elapsed milliseconds of each
  * stage to ms[3 * r + s] (record r in execution order; stage s in launch
  * order: forward N2, N1, N0 -- backward N0, N1, N2; a stage skipped for a
- * length-1 axis reads 0), stores the number of records in *count (at most
+ * length-1 axis reads 0; when the N2 and N1 stages run fused through L2, the
+ * first of the two slots holds their combined time and the second reads 0),
+ * stores the number of records in *count (at most
  * the capacity), and stops recording.  ms must hold 3 * capacity floats.
  */
 int afft_plan_timing_end(afft_plan *p, float *ms, int *count);

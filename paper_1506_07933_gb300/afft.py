@@ -39,7 +39,7 @@ EXPORTS = [
     "afft_plan_workspace_bytes", "afft_plan_input_bytes", "afft_plan_output_bytes",
     "afft_plan_launches", "afft_status_string", "afft_fill_uniform",
     "afft_plan_timing_begin", "afft_plan_timing_end", "afft_c2r_noalloc",
-    "afft_plan_device_status",
+    "afft_plan_device_status", "afft_plan_set_l2_chunk", "afft_plan_l2_chunk",
 ]
 
 _lib = None
@@ -78,10 +78,14 @@ def load(path: str = None):
     lib.afft_plan_timing_end.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(c_int)]
     lib.afft_c2r_noalloc.argtypes = [i64p, c_int, vp, vp, vp]
     lib.afft_plan_device_status.argtypes = [vp]
+    lib.afft_plan_set_l2_chunk.argtypes = [vp, sz]
+    lib.afft_plan_l2_chunk.argtypes = [vp]
+    lib.afft_plan_l2_chunk.restype = sz
     for f in ("afft_plan_create", "afft_execute_forward", "afft_execute_backward",
               "afft_execute_forward_host", "afft_execute_backward_host", "afft_plan_destroy",
               "afft_plan_launches", "afft_fill_uniform", "afft_plan_timing_begin",
-              "afft_plan_timing_end", "afft_c2r_noalloc", "afft_plan_device_status"):
+              "afft_plan_timing_end", "afft_c2r_noalloc", "afft_plan_device_status",
+              "afft_plan_set_l2_chunk"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -241,6 +245,14 @@ class Plan:
                 raise ValueError("%s must be a contiguous CPU tensor %s %s" % (w, dt, shape))
         afft_execute_backward_host(self._p, host_in.data_ptr(), host_out.data_ptr(), dev_in.data_ptr(),
                                    dev_out.data_ptr(), _stream_handle(stream))
+
+    def set_l2_chunk(self, nbytes: int) -> None:
+        """Slab size for L2-resident fusion of the N2 and N1 stages (0: unfused)."""
+        _check(load().afft_plan_set_l2_chunk(self._p, int(nbytes)), "afft_plan_set_l2_chunk")
+
+    @property
+    def l2_chunk(self) -> int:
+        return int(load().afft_plan_l2_chunk(self._p))
 
     def device_status(self) -> int:
         """Synchronises; returns 0, or 11 (AFFT_ERR_TIMEOUT) if a bounded wait ran out since the last call."""

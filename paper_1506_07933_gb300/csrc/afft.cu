@@ -48,6 +48,12 @@ struct afft_plan {
     int timing_cap;
     int timing_count;
     unsigned *d_err;       // set by a kernel whose bounded wait ran out
+    // L2-resident fusion of the N2 and N1 stages: slabs of `chunk_planes` planes,
+    // the N1 stage of slab c on a second stream while the N2 stage of slab c+1 runs
+    size_t chunk_bytes;    // requested slab size (0: off)
+    int chunk_planes;      // planes per slab; 0 when the stages run unfused
+    cudaStream_t aux;
+    std::vector<cudaEvent_t> chunk_ev;  // [0]: fork, then two per slab
 };
 
 namespace {
@@ -309,10 +315,16 @@ int plan_shapes(afft_plan *p)
 
 // --------------------------------------------------------------- execute ---
 
-cudaError_t launch(const AxisPlan &a, int which, void **args, cudaStream_t s)
+cudaError_t launch(const AxisPlan &a, int which, long long blocks, void **args, cudaStream_t s)
 {
     const Launch &L = a.launch;
-    return cudaLaunchKernel(a.ks->fn[which], dim3((unsigned)L.blocks), dim3(L.threads), args, L.smem, s);
+    if (blocks <= 0) return cudaSuccess;
+    return cudaLaunchKernel(a.ks->fn[which], dim3((unsigned)blocks), dim3(L.threads), args, L.smem, s);
+}
+
+long long line_blocks(const AxisPlan &a, long long nlines)
+{
+    return (nlines + a.launch.lines - 1) / a.launch.lines;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -387,10 +399,10 @@ cudaError_t strided(const AxisPlan &a, const V *in, V *out, const V *tw, long lo
     if (rm.in > 0) return cudaErrorInvalidValue;
     StageDesc d = a.desc;
     tw += a.tw_base;
-    long long tpo = a.launch.tiles_per_outer;
+    long long tpo = (W + a.launch.lines - 1) / a.launch.lines;
     int lg = a.launch.log2_lines;
     void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&tw, (void *)&W, (void *)&tpo, (void *)&lg};
-    return launch(a, backward ? KS_STRIDED_BWD : KS_STRIDED_FWD, args, s);
+    return launch(a, backward ? KS_STRIDED_BWD : KS_STRIDED_FWD, outer * tpo, args, s);
 }
 
 template <typename V>
@@ -403,7 +415,7 @@ cudaError_t contig(const AxisPlan &a, const V *in, V *out, const V *tw, long lon
     int lines = a.launch.lines;
     T sc = (T)scale;
     void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&tw, (void *)&nlines, (void *)&lines, (void *)&sc};
-    return launch(a, backward ? KS_CONTIG_BWD : KS_CONTIG_FWD, args, s);
+    return launch(a, backward ? KS_CONTIG_BWD : KS_CONTIG_FWD, line_blocks(a, nlines), args, s);
 }
 
 template <typename V, typename T>
@@ -414,7 +426,7 @@ cudaError_t r2c(const AxisPlan &a, const T *in, V *out, const V *tw, const V *po
     tw += a.tw_base;
     int lines = a.launch.lines;
     void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&tw, (void *)&post, (void *)&nlines, (void *)&lines};
-    return launch(a, KS_R2C, args, s);
+    return launch(a, KS_R2C, line_blocks(a, nlines), args, s);
 }
 
 template <typename V, typename T>
@@ -427,7 +439,7 @@ cudaError_t c2r(const AxisPlan &a, const V *in, T *out, const V *tw, const V *po
     T sc = (T)scale;
     void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&tw, (void *)&post, (void *)&nlines,
                     (void *)&lines, (void *)&sc};
-    return launch(a, KS_C2R, args, s);
+    return launch(a, KS_C2R, line_blocks(a, nlines), args, s);
 }
 
 // Records the timing event `i` (0..3) of the current record, if timing is on.
@@ -437,54 +449,156 @@ void mark(afft_plan *p, int i, cudaStream_t s)
     if (i == 3 && p->timing_count < p->timing_cap) ++p->timing_count;
 }
 
+// Forward: N2 stage (c2c, or r2c into the padded workspace), N1 stage, N0 stage.
+// With chunk_planes > 0 the N2 and N1 stages run slab by slab: N2 of slab c on
+// the caller's stream, N1 of slab c on the plan's second stream right after, so
+// the slab is still in L2 when N1 reads it; N2 of slab c+2 waits for N1 of slab c,
+// which bounds the data in flight to about three slabs.
 template <typename V>
 int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
-    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh, nhp = p->nhp;
+    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, nhp = p->nhp;
     // padded R2C: N2 and N1 stages in the workspace, N0 stage converts to the compact `out`
     V *o = (V *)out;
     V *w = nhp != nh ? (V *)p->d_work : o;
-    cudaError_t e;
+    const long long plane_in = n1 * n2;   // elements of `in` per plane (reals for r2c)
+    const long long plane_w = n1 * nhp;   // complex elements of w per plane
+    auto zstage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
+        if (p->kind == AFFT_C2C)
+            return contig<V>(p->ax[2], (const V *)in + p0 * plane_in, w + p0 * plane_w, tw, np * n1, 0, 1.0, st);
+        return r2c<V, T>(p->ax[2], (const T *)in + p0 * plane_in, w + p0 * plane_w, tw, tw + p->post_off,
+                         np * n1, st);
+    };
+    auto ystage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
+        if (n1 <= 1) return cudaSuccess;
+        return strided<V>(p->ax[1], w + p0 * plane_w, w + p0 * plane_w, tw, np, nhp, 0, st, p->d_err);
+    };
+    cudaError_t e = cudaSuccess;
     mark(p, 0, s);
-    if (p->kind == AFFT_C2C) e = contig<V>(p->ax[2], (const V *)in, o, tw, n0 * n1, 0, 1.0, s);
-    else e = r2c<V, T>(p->ax[2], (const T *)in, w, tw, tw + p->post_off, n0 * n1, s);
-    if (e != cudaSuccess) return AFFT_ERR_CUDA;
-    mark(p, 1, s);
-    if (n1 > 1 && (e = strided<V>(p->ax[1], w, w, tw, n0, nhp, 0, s, p->d_err)) != cudaSuccess)
-        return AFFT_ERR_CUDA;
-    mark(p, 2, s);
+    const int K = p->chunk_planes;
+    if (K > 0) {
+        const long long C = (n0 + K - 1) / K;
+        cudaEvent_t *ev = p->chunk_ev.data();
+        if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return AFFT_ERR_CUDA;
+        if ((e = cudaStreamWaitEvent(p->aux, ev[0], 0)) != cudaSuccess) return AFFT_ERR_CUDA;
+        for (long long c = 0; c < C && e == cudaSuccess; ++c) {
+            const long long p0 = c * K, np = std::min<long long>(K, n0 - p0);
+            if (c >= 2) e = cudaStreamWaitEvent(s, ev[1 + 2 * (c - 2) + 1], 0);
+            if (e == cudaSuccess) e = zstage(p0, np, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1 + 2 * c], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, ev[1 + 2 * c], 0);
+            if (e == cudaSuccess) e = ystage(p0, np, p->aux);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1 + 2 * c + 1], p->aux);
+        }
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1 + 2 * (C - 1) + 1], 0);
+        if (e != cudaSuccess) return AFFT_ERR_CUDA;
+        mark(p, 1, s);
+        mark(p, 2, s);
+    } else {
+        if (zstage(0, n0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        mark(p, 1, s);
+        if (ystage(0, n0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        mark(p, 2, s);
+    }
     if (n0 > 1) {
         const Remap rm = nhp != nh ? Remap{n1 * nh, (int)nhp, (int)nh} : Remap{0, 0, 0};
-        if ((e = strided<V>(p->ax[0], w, o, tw, 1, n1 * nhp, 0, s, p->d_err, rm)) != cudaSuccess)
+        if (strided<V>(p->ax[0], w, o, tw, 1, n1 * nhp, 0, s, p->d_err, rm) != cudaSuccess) return AFFT_ERR_CUDA;
+    } else if (w != o) {
+        // one plane: the compact output is the padded workspace without its pad column
+        if (cudaMemcpy2DAsync(o, nh * sizeof(V), w, nhp * sizeof(V), nh * sizeof(V), n1, cudaMemcpyDeviceToDevice,
+                              s) != cudaSuccess)
             return AFFT_ERR_CUDA;
     }
     mark(p, 3, s);
     return AFFT_OK;
 }
 
+// Backward: N0 stage (into the workspace for r2c plans), N1 stage, N2 stage
+// (c2c with x 1/N, or c2r), fused slab by slab through L2 like the forward.
 template <typename V>
 int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
-    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh, nhp = p->nhp;
+    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, nhp = p->nhp;
     const double scale = 1.0 / ((double)p->n[0] * (double)p->n[1] * (double)p->n[2]);
     // C2C works in `out`; c2r works in the plan's workspace and writes real `out` last.
     V *buf = p->kind == AFFT_C2C ? (V *)out : (V *)p->d_work;
+    const long long plane_w = n1 * nhp, plane_out = n1 * n2;
+    auto ystage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
+        if (n1 <= 1) return cudaSuccess;
+        return strided<V>(p->ax[1], buf + p0 * plane_w, buf + p0 * plane_w, tw, np, nhp, 1, st, p->d_err);
+    };
+    auto zstage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
+        if (p->kind == AFFT_C2C)
+            return contig<V>(p->ax[2], buf + p0 * plane_w, (V *)out + p0 * plane_out, tw, np * n1, 1, scale, st);
+        return c2r<V, T>(p->ax[2], buf + p0 * plane_w, (T *)out + p0 * plane_out, tw, tw + p->post_off, np * n1,
+                         scale, st);
+    };
     mark(p, 0, s);
     const Remap rm = nhp != nh ? Remap{n1 * nhp, (int)nh, (int)nhp} : Remap{0, 0, 0};
-    cudaError_t e = strided<V>(p->ax[0], (const V *)in, buf, tw, 1, n1 * nh, 1, s, p->d_err, rm);
-    if (e != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n0 > 1 || nhp == nh) {
+        if (strided<V>(p->ax[0], (const V *)in, buf, tw, 1, n1 * nh, 1, s, p->d_err, rm) != cudaSuccess)
+            return AFFT_ERR_CUDA;
+    } else {
+        if (cudaMemcpy2DAsync(buf, nhp * sizeof(V), in, nh * sizeof(V), nh * sizeof(V), n1, cudaMemcpyDeviceToDevice,
+                              s) != cudaSuccess)
+            return AFFT_ERR_CUDA;
+    }
     mark(p, 1, s);
-    if (n1 > 1 && (e = strided<V>(p->ax[1], buf, buf, tw, n0, nhp, 1, s, p->d_err)) != cudaSuccess)
-        return AFFT_ERR_CUDA;
-    mark(p, 2, s);
-    if (p->kind == AFFT_C2C) e = contig<V>(p->ax[2], buf, (V *)out, tw, n0 * n1, 1, scale, s);
-    else e = c2r<V, T>(p->ax[2], buf, (T *)out, tw, tw + p->post_off, n0 * n1, scale, s);
-    if (e != cudaSuccess) return AFFT_ERR_CUDA;
+    const int K = p->chunk_planes;
+    if (K > 0) {
+        const long long C = (n0 + K - 1) / K;
+        cudaEvent_t *ev = p->chunk_ev.data();
+        cudaError_t e = cudaEventRecord(ev[0], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, ev[0], 0);
+        for (long long c = 0; c < C && e == cudaSuccess; ++c) {
+            const long long p0 = c * K, np = std::min<long long>(K, n0 - p0);
+            if (c >= 2) e = cudaStreamWaitEvent(s, ev[1 + 2 * (c - 2) + 1], 0);
+            if (e == cudaSuccess) e = ystage(p0, np, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1 + 2 * c], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, ev[1 + 2 * c], 0);
+            if (e == cudaSuccess) e = zstage(p0, np, p->aux);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[1 + 2 * c + 1], p->aux);
+        }
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1 + 2 * (C - 1) + 1], 0);
+        if (e != cudaSuccess) return AFFT_ERR_CUDA;
+        mark(p, 2, s);
+    } else {
+        if (ystage(0, n0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        mark(p, 2, s);
+        if (zstage(0, n0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    }
     mark(p, 3, s);
+    return AFFT_OK;
+}
+
+// Chooses the slab size for L2-resident N2/N1 fusion and creates the second
+// stream and the events it needs (host-side objects; no device memory).
+int configure_chunks(afft_plan *p, size_t bytes)
+{
+    p->chunk_bytes = bytes;
+    p->chunk_planes = 0;
+    const long long n0 = p->n[0], n1 = p->n[1];
+    const size_t plane = (size_t)n1 * p->nhp * cplx_size(p->precision);
+    if (bytes == 0 || n1 <= 1 || n0 < 3 || plane == 0) return AFFT_OK;
+    long long K = (long long)(bytes / plane);
+    if (K < 1) K = 1;
+    if (K * 2 >= n0) return AFFT_OK;  // fewer than three slabs: nothing to gain
+    const long long C = (n0 + K - 1) / K;
+    if (!p->aux && cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess) {
+        p->aux = nullptr;
+        return AFFT_ERR_CUDA;
+    }
+    const size_t need = (size_t)(1 + 2 * C);
+    while (p->chunk_ev.size() < need) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return AFFT_ERR_CUDA;
+        p->chunk_ev.push_back(ev);
+    }
+    p->chunk_planes = (int)K;
     return AFFT_OK;
 }
 
@@ -666,6 +780,8 @@ int afft_plan_destroy(afft_plan *p)
         if (p->d_err) cudaFree(p->d_err);
     }
     for (cudaEvent_t ev : p->events) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : p->chunk_ev) cudaEventDestroy(ev);
+    if (p->aux) cudaStreamDestroy(p->aux);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
     return st;
@@ -730,8 +846,28 @@ size_t afft_plan_output_bytes(const afft_plan *p) { return p ? out_bytes(p) : 0;
 int afft_plan_launches(const afft_plan *p, int backward)
 {
     if (!p) return 0;
-    if (backward) return 2 + (p->n[1] > 1 ? 1 : 0);
-    return 1 + (p->n[1] > 1 ? 1 : 0) + (p->n[0] > 1 ? 1 : 0);
+    const long long slabs = p->chunk_planes > 0 ? (p->n[0] + p->chunk_planes - 1) / p->chunk_planes : 1;
+    const int y = p->n[1] > 1 ? 1 : 0;
+    if (backward) return (int)(1 + slabs * (1 + y));
+    const int x = p->n[0] > 1 ? 1 : 0;
+    return (int)(slabs * (1 + y) + x);
+}
+
+int afft_plan_set_l2_chunk(afft_plan *p, size_t bytes)
+{
+    if (!p) return AFFT_ERR_NULL;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    const int st = configure_chunks(p, bytes);
+    if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
+    return st;
+}
+
+size_t afft_plan_l2_chunk(const afft_plan *p)
+{
+    if (!p || p->chunk_planes <= 0) return 0;
+    return (size_t)p->chunk_planes * (size_t)p->n[1] * p->nhp * cplx_size(p->precision);
 }
 
 int afft_fill_uniform(void *dev_out, int64_t count, uint64_t seed, int precision, void *stream)
