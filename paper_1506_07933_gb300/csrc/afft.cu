@@ -29,6 +29,16 @@ struct AxisPlan {
     int pipe_slots;        // CTAs resident at once (SMs x CTAs per SM): the persistent grid's cap
 };
 
+// Four-step split of one axis whose lines are longer than a CTA holds
+// (n = n_a n_b): the axis plan ax[a] runs the length-n_b DFTs along j_b (stride
+// n_a W), then `a` runs the twiddle + length-n_a DFT + transposed store.
+struct FourStep {
+    bool on;
+    int na, nb;
+    AxisPlan a;            // length n_a, generic family's k_fourstep
+    int wn_base;           // offset of w_n^m, m < n, in the twiddle table
+};
+
 struct afft_plan {
     int64_t n[3];
     int kind;
@@ -50,6 +60,8 @@ struct afft_plan {
     unsigned *d_err;       // set by a kernel whose bounded wait ran out
     // L2-resident fusion of the N2 and N1 stages: slabs of `chunk_planes` planes,
     // the N1 stage of slab c on a second stream while the N2 stage of slab c+1 runs
+    FourStep four[3];      // per axis
+    void *d_four;          // four-step intermediate: n0*n1*nhp complex
     size_t chunk_bytes;    // requested slab size (0: off)
     int chunk_planes;      // planes per slab; 0 when the stages run unfused
     cudaStream_t aux;
@@ -85,6 +97,23 @@ std::vector<int> radix_plan(int64_t n)
     while (n % 3 == 0) { n /= 3; r.push_back(3); }
     while (n % 5 == 0) { n /= 5; r.push_back(5); }
     return r;
+}
+
+// n = n_a n_b with both factors at most kMaxLine, n_a the largest such factor
+// not above sqrt(n); false if no split exists.
+bool four_step_split(int64_t n, int &na, int &nb)
+{
+    for (int64_t a = (int64_t)std::sqrt((double)n) + 1; a >= 1; --a) {
+        if (a * a > n || n % a != 0) continue;
+        const int64_t b = n / a;
+        if (a <= kMaxLine && b <= kMaxLine) {
+            na = (int)a;
+            nb = (int)b;
+            return true;
+        }
+        return false;  // the other factor only grows for smaller a
+    }
+    return false;
 }
 
 const KernelSet *lookup_kernels(int precision, int64_t n)
@@ -269,8 +298,10 @@ int plan_shapes(afft_plan *p)
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh;
-    // strided stages: persistent double-buffered kernels where the family has them
-    for (int a = 0; a < 2; ++a) {
+    // strided stages (and the first half of a four-step contiguous axis): persistent
+    // double-buffered kernels where the family has them
+    for (int a = 0; a < 3; ++a) {
+        if (a == 2 && !p->four[2].on) continue;
         AxisPlan &ap = p->ax[a];
         ap.pipe = false;
         const KernelSet *ks = ap.ks;
@@ -290,7 +321,8 @@ int plan_shapes(afft_plan *p)
     // which TMA needs; keep the N2 and N1 stages in a workspace with rows of nh + 1 and let the
     // (pipelined) N0 stage convert between that and the compact layout.
     p->nhp = nh;
-    if (p->kind == AFFT_R2C && elem == 8 && (nh % 2) == 1 && n0 > 1 && p->ax[0].pipe) p->nhp = nh + 1;
+    if (p->kind == AFFT_R2C && elem == 8 && (nh % 2) == 1 && n0 > 1 && p->ax[0].pipe && !p->four[0].on)
+        p->nhp = nh + 1;
     p->ax[2].desc.ld = p->nhp != nh ? (int)p->nhp : 0;
     const long long nhp = p->nhp;
     // Specialised kernels run two CTAs per SM: keep their tiles to half the SM.
@@ -298,12 +330,31 @@ int plan_shapes(afft_plan *p)
         return a.ks->generic ? (size_t)max_smem : (size_t)std::min(max_smem, 112 * 1024);
     };
     AxisPlan &z = p->ax[2], &y = p->ax[1], &x = p->ax[0];
-    if (!shape_contig(z.desc, n0 * n1, elem, z.ks->max_threads, budget(z), z.launch))
-        return AFFT_ERR_UNSUPPORTED;
-    if (!shape_strided(y.desc, n0, nhp, elem, y.ks->max_threads, budget(y), y.launch))
-        return AFFT_ERR_UNSUPPORTED;
-    if (!shape_strided(x.desc, 1, n1 * nh, elem, x.ks->max_threads, budget(x), x.launch))
-        return AFFT_ERR_UNSUPPORTED;
+    // width of each axis' lines (W of its [outer][n][W] view); a four-step axis runs
+    // its first half with W * n_a
+    const long long outer[3] = {1, n0, n0 * n1};
+    const long long width[3] = {n1 * nh, nhp, 1};
+    for (int a = 0; a < 3; ++a) {
+        const FourStep &f = p->four[a];
+        AxisPlan &ap = p->ax[a];
+        bool ok;
+        if (a == 2 && !f.on) ok = shape_contig(z.desc, n0 * n1, elem, z.ks->max_threads, budget(z), z.launch);
+        else ok = shape_strided(ap.desc, outer[a], width[a] * (f.on ? f.na : 1), elem, ap.ks->max_threads,
+                                budget(ap), ap.launch);
+        if (!ok) return AFFT_ERR_UNSUPPORTED;
+        if (f.on) {
+            AxisPlan &fa = p->four[a].a;
+            if (!shape_strided(fa.desc, outer[a] * f.nb, width[a], elem, fa.ks->max_threads, (size_t)max_smem,
+                               fa.launch))
+                return AFFT_ERR_UNSUPPORTED;
+            for (int k = 0; k < 2; ++k)
+                if (cudaFuncSetAttribute(fa.ks->four[k], cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) !=
+                    cudaSuccess)
+                    return AFFT_ERR_CUDA;
+        }
+    }
+    (void)x;
+    (void)y;
     for (int a = 0; a < 3; ++a)
         for (int k = 0; k < KS_COUNT; ++k) {
             const cudaError_t e = cudaFuncSetAttribute(p->ax[a].ks->fn[k],
@@ -405,6 +456,27 @@ cudaError_t strided(const AxisPlan &a, const V *in, V *out, const V *tw, long lo
     return launch(a, backward ? KS_STRIDED_BWD : KS_STRIDED_FWD, outer * tpo, args, s);
 }
 
+// Second half of a four-step axis: twiddle, length-n_a DFTs, transposed store.
+template <typename V>
+cudaError_t fourstep(const FourStep &f, const V *in, V *out, const V *tw, long long outer, long long W,
+                     int backward, double scale, cudaStream_t s)
+{
+    using T = decltype(V().x);
+    const AxisPlan &a = f.a;
+    StageDesc d = a.desc;
+    const V *twa = tw + a.tw_base;
+    const V *wn = tw + f.wn_base;
+    long long tpo = (W + a.launch.lines - 1) / a.launch.lines;
+    int lg = a.launch.log2_lines, nb = f.nb;
+    T sc = (T)scale;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&twa, (void *)&wn, (void *)&W, (void *)&tpo,
+                    (void *)&lg, (void *)&nb, (void *)&sc};
+    const long long blocks = outer * f.nb * tpo;
+    if (blocks <= 0) return cudaSuccess;
+    return cudaLaunchKernel(a.ks->four[backward ? 1 : 0], dim3((unsigned)blocks), dim3(a.launch.threads), args,
+                            a.launch.smem, s);
+}
+
 template <typename V>
 cudaError_t contig(const AxisPlan &a, const V *in, V *out, const V *tw, long long nlines, int backward,
                    double scale, cudaStream_t s)
@@ -449,6 +521,24 @@ void mark(afft_plan *p, int i, cudaStream_t s)
     if (i == 3 && p->timing_count < p->timing_cap) ++p->timing_count;
 }
 
+// One axis stage over a [outer][n][W] view from `in` to `out` (in place when
+// equal): a strided stage, or the two halves of a four-step split through the
+// plan's four-step buffer.  `scale` multiplies the result (four-step only;
+// unsplit strided stages are never the scaled last stage).
+template <typename V>
+cudaError_t axis_stage(afft_plan *p, int a, const V *in, V *out, long long outer, long long W, int backward,
+                       double scale, cudaStream_t s, const Remap &rm = Remap{0, 0, 0})
+{
+    const V *tw = (const V *)p->d_tw;
+    const FourStep &f = p->four[a];
+    if (!f.on) return strided<V>(p->ax[a], in, out, tw, outer, W, backward, s, p->d_err, rm);
+    if (rm.in > 0) return cudaErrorInvalidValue;
+    V *tmp = (V *)p->d_four;
+    cudaError_t e = strided<V>(p->ax[a], in, tmp, tw, outer, W * f.na, backward, s, p->d_err);
+    if (e != cudaSuccess) return e;
+    return fourstep<V>(f, tmp, out, tw, outer, W, backward, scale, s);
+}
+
 // Forward: N2 stage (c2c, or r2c into the padded workspace), N1 stage, N0 stage.
 // With chunk_planes > 0 the N2 and N1 stages run slab by slab: N2 of slab c on
 // the caller's stream, N1 of slab c on the plan's second stream right after, so
@@ -466,6 +556,8 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
     const long long plane_in = n1 * n2;   // elements of `in` per plane (reals for r2c)
     const long long plane_w = n1 * nhp;   // complex elements of w per plane
     auto zstage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
+        if (p->kind == AFFT_C2C && p->four[2].on)
+            return axis_stage<V>(p, 2, (const V *)in + p0 * plane_in, w + p0 * plane_w, np * n1, 1, 0, 1.0, st);
         if (p->kind == AFFT_C2C)
             return contig<V>(p->ax[2], (const V *)in + p0 * plane_in, w + p0 * plane_w, tw, np * n1, 0, 1.0, st);
         return r2c<V, T>(p->ax[2], (const T *)in + p0 * plane_in, w + p0 * plane_w, tw, tw + p->post_off,
@@ -473,7 +565,7 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
     };
     auto ystage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
         if (n1 <= 1) return cudaSuccess;
-        return strided<V>(p->ax[1], w + p0 * plane_w, w + p0 * plane_w, tw, np, nhp, 0, st, p->d_err);
+        return axis_stage<V>(p, 1, w + p0 * plane_w, w + p0 * plane_w, np, nhp, 0, 1.0, st);
     };
     cudaError_t e = cudaSuccess;
     mark(p, 0, s);
@@ -504,7 +596,7 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
     }
     if (n0 > 1) {
         const Remap rm = nhp != nh ? Remap{n1 * nh, (int)nhp, (int)nh} : Remap{0, 0, 0};
-        if (strided<V>(p->ax[0], w, o, tw, 1, n1 * nhp, 0, s, p->d_err, rm) != cudaSuccess) return AFFT_ERR_CUDA;
+        if (axis_stage<V>(p, 0, w, o, 1, n1 * nhp, 0, 1.0, s, rm) != cudaSuccess) return AFFT_ERR_CUDA;
     } else if (w != o) {
         // one plane: the compact output is the padded workspace without its pad column
         if (cudaMemcpy2DAsync(o, nh * sizeof(V), w, nhp * sizeof(V), nh * sizeof(V), n1, cudaMemcpyDeviceToDevice,
@@ -529,9 +621,11 @@ int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
     const long long plane_w = n1 * nhp, plane_out = n1 * n2;
     auto ystage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
         if (n1 <= 1) return cudaSuccess;
-        return strided<V>(p->ax[1], buf + p0 * plane_w, buf + p0 * plane_w, tw, np, nhp, 1, st, p->d_err);
+        return axis_stage<V>(p, 1, buf + p0 * plane_w, buf + p0 * plane_w, np, nhp, 1, 1.0, st);
     };
     auto zstage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
+        if (p->kind == AFFT_C2C && p->four[2].on)
+            return axis_stage<V>(p, 2, buf + p0 * plane_w, (V *)out + p0 * plane_out, np * n1, 1, 1, scale, st);
         if (p->kind == AFFT_C2C)
             return contig<V>(p->ax[2], buf + p0 * plane_w, (V *)out + p0 * plane_out, tw, np * n1, 1, scale, st);
         return c2r<V, T>(p->ax[2], buf + p0 * plane_w, (T *)out + p0 * plane_out, tw, tw + p->post_off, np * n1,
@@ -540,7 +634,7 @@ int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
     mark(p, 0, s);
     const Remap rm = nhp != nh ? Remap{n1 * nhp, (int)nh, (int)nhp} : Remap{0, 0, 0};
     if (n0 > 1 || nhp == nh) {
-        if (strided<V>(p->ax[0], (const V *)in, buf, tw, 1, n1 * nh, 1, s, p->d_err, rm) != cudaSuccess)
+        if (axis_stage<V>(p, 0, (const V *)in, buf, 1, n1 * nh, 1, 1.0, s, rm) != cudaSuccess)
             return AFFT_ERR_CUDA;
     } else {
         if (cudaMemcpy2DAsync(buf, nhp * sizeof(V), in, nh * sizeof(V), nh * sizeof(V), n1, cudaMemcpyDeviceToDevice,
@@ -666,7 +760,15 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
     if (kind == AFFT_R2C && n[2] % 2 != 0) return AFFT_ERR_R2C_ODD;
     if (precision == AFFT_F32_SPLIT) return AFFT_ERR_UNSUPPORTED;
     const int64_t zlen = kind == AFFT_R2C ? n[2] / 2 : n[2];
-    if (n[0] > kMaxLine || n[1] > kMaxLine || zlen > kMaxLine) return AFFT_ERR_UNSUPPORTED;
+    // lines longer than one CTA holds are split four-step (n = n_a n_b, both <= kMaxLine);
+    // the contiguous axis of an r2c plan is not split
+    if (kind == AFFT_R2C && zlen > kMaxLine) return AFFT_ERR_UNSUPPORTED;
+    int split_a[3] = {0, 0, 0}, split_b[3] = {0, 0, 0};
+    {
+        const int64_t len0[3] = {n[0], n[1], zlen};
+        for (int a = 0; a < 3; ++a)
+            if (len0[a] > kMaxLine && !four_step_split(len0[a], split_a[a], split_b[a])) return AFFT_ERR_UNSUPPORTED;
+    }
 
     afft_plan *p = new (std::nothrow) afft_plan();
     if (!p) return AFFT_ERR_NOMEM;
@@ -681,10 +783,27 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
 
     std::vector<int> tm, tl;
     const int64_t len[3] = {n[0], n[1], zlen};
+    bool any_four = false;
     for (int a = 0; a < 3; ++a) {
-        p->ax[a].ks = lookup_kernels(precision, len[a]);
+        FourStep &f = p->four[a];
+        f.on = split_a[a] > 0;
+        const int64_t first = f.on ? split_b[a] : len[a];   // the first (or only) DFT length
+        p->ax[a].ks = lookup_kernels(precision, first);
         p->ax[a].tw_base = (int)tm.size();
-        build_desc(len[a], p->ax[a].ks, p->ax[a].desc, tm, tl);
+        build_desc(first, p->ax[a].ks, p->ax[a].desc, tm, tl);
+        if (f.on) {
+            any_four = true;
+            f.na = split_a[a];
+            f.nb = split_b[a];
+            f.a.ks = precision == AFFT_F64 ? generic_kernels_f64() : generic_kernels_f32();
+            f.a.tw_base = (int)tm.size();
+            build_desc(f.na, f.a.ks, f.a.desc, tm, tl);
+            f.wn_base = (int)tm.size();
+            for (int64_t m = 0; m < len[a]; ++m) {
+                tm.push_back((int)m);
+                tl.push_back((int)len[a]);
+            }
+        }
     }
     p->post_off = (int)tm.size();
     if (kind == AFFT_R2C) {
@@ -703,6 +822,13 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
             st = AFFT_ERR_NOMEM;
         } else if (cudaMemset(p->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
             st = AFFT_ERR_CUDA;
+        }
+    }
+    if (st == AFFT_OK && any_four) {
+        const size_t bytes = (size_t)n[0] * n[1] * p->nhp * cplx_size(precision);
+        if (cudaMalloc(&p->d_four, bytes) != cudaSuccess) {
+            p->d_four = nullptr;
+            st = AFFT_ERR_NOMEM;
         }
     }
     if (st == AFFT_OK && kind == AFFT_R2C) {
@@ -773,11 +899,12 @@ int afft_plan_destroy(afft_plan *p)
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     int st = AFFT_OK;
-    if (p->d_tw || p->d_work || p->d_err) {
+    if (p->d_tw || p->d_work || p->d_err || p->d_four) {
         if (cudaDeviceSynchronize() != cudaSuccess) st = AFFT_ERR_CUDA;
         if (p->d_tw) cudaFree(p->d_tw);
         if (p->d_work) cudaFree(p->d_work);
         if (p->d_err) cudaFree(p->d_err);
+        if (p->d_four) cudaFree(p->d_four);
     }
     for (cudaEvent_t ev : p->events) cudaEventDestroy(ev);
     for (cudaEvent_t ev : p->chunk_ev) cudaEventDestroy(ev);
@@ -847,10 +974,11 @@ int afft_plan_launches(const afft_plan *p, int backward)
 {
     if (!p) return 0;
     const long long slabs = p->chunk_planes > 0 ? (p->n[0] + p->chunk_planes - 1) / p->chunk_planes : 1;
-    const int y = p->n[1] > 1 ? 1 : 0;
-    if (backward) return (int)(1 + slabs * (1 + y));
-    const int x = p->n[0] > 1 ? 1 : 0;
-    return (int)(slabs * (1 + y) + x);
+    const int f0 = p->four[0].on, f1 = p->four[1].on, f2 = p->four[2].on && p->kind == AFFT_C2C;
+    const int y = p->n[1] > 1 ? 1 + f1 : 0;
+    if (backward) return (int)(1 + f0 + slabs * (1 + f2 + y));
+    const int x = p->n[0] > 1 ? 1 + f0 : 0;
+    return (int)(slabs * (1 + f2 + y) + x);
 }
 
 int afft_plan_set_l2_chunk(afft_plan *p, size_t bytes)

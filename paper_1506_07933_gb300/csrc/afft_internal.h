@@ -87,6 +87,10 @@ struct KernelSet {
     int max_threads;               // largest CTA the kernels were compiled for
     bool generic;
     const void *pipe[PIPE_COUNT];  // null when the family has no pipelined strided kernel
+    // generic family only: second half of a four-step line, (const V *in, V *out,
+    // StageDesc d, const V *tw, const V *wn, long long W, long long tiles_per_outer,
+    // int log2_lines, int nb, T scale); [0] forward, [1] backward
+    const void *four[2];
     int pipe_lines;                // columns per tile of the pipelined kernel
     int pipe_threads;              // its (compile-time) CTA size
     int pipe_smem;                 // its dynamic shared memory (two tile buffers)

@@ -119,4 +119,35 @@ template <typename V> struct C2RPre {
 };
 
 
+// Four-step split of a line of n = n_a n_b points (j = n_a j_b + j_a,
+// k = k_b + n_b k_a): after length-n_b DFTs along j_b, element (j_a, k_b) is
+// multiplied by w_n^{j_a k_b} and length-n_a DFTs run along j_a.  FourStepSrc
+// reads row j_a of the tile for one k_b and applies that twiddle (conjugated
+// for the backward transform); FourStepDst stores DFT output k_a to row
+// k_b + n_b k_a of the destination line (the transpose back to natural order).
+template <int S, typename V> struct FourStepSrc {
+    const V *base;                 // &t[o'][0][c0], o' = (o, k_b)
+    long long W;
+    int valid;
+    const V *wn;                   // w_n^m, m < n (forward sign)
+    int kb;
+    __device__ __forceinline__ V operator()(int l, int p) const
+    {
+        if (l >= valid) return czero<V>();
+        const V v = base[(long long)p * W + l];
+        const V w = __ldg(wn + p * kb);   // p * kb < n_a n_b = n
+        return S < 0 ? cmul(v, w) : cmulc(v, w);
+    }
+};
+template <typename V> struct FourStepDst {
+    V *base;                       // &y[o][k_b][c0]
+    long long Wrow;                // n_b * W: distance between rows k_a and k_a + 1
+    int valid;
+    typename RealOf<V>::T scale;
+    __device__ __forceinline__ void operator()(int l, int p, V v) const
+    {
+        if (l < valid) base[(long long)p * Wrow + l] = cscale(v, scale);
+    }
+};
+
 }  // namespace afft

@@ -376,6 +376,10 @@ template <class F, typename V> KernelSet kernel_set(int n, int npass, const int 
     k.fn[KS_C2R] = (const void *)k_c2r<F, V>;
     k.max_threads = F::template threads<V>();
     k.generic = F::generic;
+    if constexpr (F::generic) {
+        k.four[0] = (const void *)k_fourstep<-1, V>;
+        k.four[1] = (const void *)k_fourstep<+1, V>;
+    }
     if constexpr (!F::generic) {
         // n = 1024 would need 64-byte tile rows to double-buffer; measured slower than the
         // single-buffered kernel with the same rows, so it keeps the non-pipelined kernel.

@@ -345,6 +345,30 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     }
 }
 
+// Second half of a four-step line (see FourStepSrc): the input is
+// [outer * n_b][n_a][W] (row k_b of each outer line group holds the length-n_b
+// DFT outputs, laid out as n_a rows), the output [outer][n_a n_b][W].  Generic
+// family only: the split serves lines longer than one CTA holds.
+template <int S, typename V>
+__global__ void __launch_bounds__(256, 1)
+    k_fourstep(const V *__restrict__ in, V *out, const __grid_constant__ StageDesc d, const V *__restrict__ tw,
+               const V *__restrict__ wn, long long W, long long tiles_per_outer, int log2_lines, int nb,
+               typename RealOf<V>::T scale)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *sm = reinterpret_cast<V *>(smem_raw);
+    const int na = d.n;
+    const int lines = 1 << log2_lines;
+    const long long op = blockIdx.x / tiles_per_outer;            // (o, k_b)
+    const long long c0 = (blockIdx.x - op * tiles_per_outer) * lines;
+    const long long o = op / nb;
+    const int kb = (int)(op - o * nb);
+    const int valid = (int)min((long long)lines, W - c0);
+    const FourStepSrc<S, V> src{in + op * (long long)na * W + c0, W, valid, wn, kb};
+    const FourStepDst<V> dst{out + (o * (long long)na * nb + kb) * W + c0, (long long)nb * W, valid, scale};
+    run_generic<S, true, false>(d, tw, sm, lines, log2_lines, MapLineFast{log2_lines}, src, dst);
+}
+
 // Line lengths with specialised kernels and their radix sequences (n first,
 // then the radices in pass order).
 #define AFFT_LINE_PLANS(X)                                                                          \

@@ -53,7 +53,7 @@ def _create(lib, n, kind, prec):
     ((8, 8, 8), 5, 0, 4),        # kind
     ((8, 8, 8), 0, 7, 5),        # precision
     ((8, 8, 8), 0, 2, 9),        # split precision: not in this version
-    ((8, 8, 8192), 0, 0, 9),     # longer line than one CTA holds
+    ((8, 8, 3 ** 15), 0, 0, 9),  # no split into two factors <= 4096
     ((8, 8, 16384), 1, 1, 9),    # r2c half length 8192
 ])
 def test_plan_create_rejects_bad_arguments(lib, n, kind, prec, code):

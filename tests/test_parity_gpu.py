@@ -413,3 +413,28 @@ def test_l2_fused_slabs_match_unfused(shape, kind, prec, planes):
         assert torch.equal(f, ref_f) and torch.equal(b, ref_b)
     ref = oracle.r2c(x) if kind == "r2c" else oracle.c2c(x)
     report("fused %s %s %s planes=%d" % (shape, kind, prec, planes), oracle.rel_l2(f.cpu().numpy(), ref), TOL[prec])
+
+
+@pytest.mark.parametrize("shape", [(8192, 2, 3), (2, 8192, 3), (2, 3, 8192), (3, 2, 6000), (1, 2, 65536),
+                                   (5000, 3, 4)])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_four_step_long_lines_c2c(shape, prec):
+    """Lines longer than 4096 points are split n = n_a n_b (four-step, with the twiddle and
+    transposed store fused into the second half) on every axis."""
+    x = synth.uniform_complex(shape, 51).astype(CDT[prec])
+    ref = oracle.c2c(x, -1, "fft")
+    report("four-step c2c %s %s fwd" % (shape, prec), oracle.rel_l2(gpu_c2c(x, prec), ref), TOL[prec])
+    R = ref.astype(CDT[prec])
+    report("four-step c2c %s %s bwd" % (shape, prec), oracle.rel_l2(gpu_c2c(R, prec, +1), oracle.c2c(R, +1, "fft")),
+           TOL[prec])
+
+
+@pytest.mark.parametrize("shape", [(8192, 4, 16), (4, 10000, 8), (6000, 2, 36)])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_four_step_long_lines_r2c(shape, prec):
+    x = synth.uniform_real(shape, 52).astype(RDT[prec])
+    ref = oracle.r2c(x)
+    report("four-step r2c %s %s" % (shape, prec), oracle.rel_l2(gpu_r2c(x, prec), ref), TOL[prec])
+    H = ref.astype(CDT[prec])
+    report("four-step c2r %s %s" % (shape, prec), oracle.rel_l2(gpu_c2r(H, shape, prec), oracle.c2r(H, shape[2])),
+           TOL[prec])
