@@ -145,16 +145,21 @@ def dft_bins(x, ks, nthreads=None) -> np.ndarray:
 
 
 def rel_l2(y, ref) -> float:
-    """||y - ref||_2 / ||ref||_2 with float64 pairwise sums, in chunks of 2**24 values."""
+    """||y - ref||_2 / ||ref||_2 with float64 pairwise sums, in chunks of 2**24 values
+    (both arrays divided by max|ref| first, so that squares neither overflow nor underflow)."""
     y = np.asarray(y).ravel()
     ref = np.asarray(ref).ravel()
     if y.shape != ref.shape:
         raise ValueError("shape mismatch %s vs %s" % (y.shape, ref.shape))
     num = den = 0.0
     step = 1 << 24
+    scale = 0.0
     for i in range(0, ref.size, step):
-        r = ref[i:i + step].astype(np.complex128)
-        d = y[i:i + step].astype(np.complex128) - r
+        scale = max(scale, float(np.max(np.abs(ref[i:i + step]))) if ref[i:i + step].size else 0.0)
+    scale = scale if scale > 0 and np.isfinite(scale) else 1.0
+    for i in range(0, ref.size, step):
+        r = ref[i:i + step].astype(np.complex128) / scale
+        d = y[i:i + step].astype(np.complex128) / scale - r
         num += float(np.sum(d.real * d.real + d.imag * d.imag))
         den += float(np.sum(r.real * r.real + r.imag * r.imag))
     if den == 0:

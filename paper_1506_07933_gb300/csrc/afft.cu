@@ -50,6 +50,7 @@ struct afft_plan {
     AxisPlan ax[3];        // ax[2] transforms the contiguous axis (length n2, or n2/2 for R2C)
     int post_off;          // R2C: offset of the w_{n2}^k table (n2/2+1 entries)
     void *d_tw;            // twiddle tables (float2 or double2)
+    void *d_twdf;          // FP64 plans: the same tables in float-float (16 bytes per entry)
     void *d_work;          // R2C workspace: n0*n1*nhp complex
     size_t work_bytes;
     int device;
@@ -239,6 +240,17 @@ __global__ void k_twiddles(const int *__restrict__ m, const int *__restrict__ L,
     v.x = (decltype(v.x))c;
     v.y = (decltype(v.y))(-s);
     out[i] = v;
+}
+
+// Float-float copy of an FP64 twiddle table: hi = fl(w), lo = fl(w - hi)
+// (plan-time FP64 arithmetic), stored as (re.hi, re.lo, im.hi, im.lo).
+__global__ void k_twiddles_df(const double2 *__restrict__ w, float4 *out, int count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double2 v = w[i];
+    const float rh = (float)v.x, ih = (float)v.y;
+    out[i] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
 }
 
 // splitmix64 (Steele, Lea, Flood 2014) as a counter-based hash.
@@ -433,9 +445,10 @@ cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, lo
     long long nt = outer * tpo;
     long long wout = rm.in > 0 ? rm.Wout : W;
     int rin = rm.in, rout = rm.out;
+    const void *twdf = a.desc.twdf;
     const unsigned grid = (unsigned)std::min<long long>(nt, a.pipe_slots);
     void *args[] = {(void *)&in, (void *)&out, (void *)&map, (void *)&tw, (void *)&W, (void *)&tpo, (void *)&nt,
-                    (void *)&err, (void *)&wout, (void *)&rin, (void *)&rout};
+                    (void *)&err, (void *)&wout, (void *)&rin, (void *)&rout, (void *)&twdf};
     return cudaLaunchKernel(a.ks->pipe[which], dim3(grid), dim3(a.ks->pipe_threads), args,
                             (size_t)a.ks->pipe_smem, s);
 }
@@ -824,6 +837,20 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
             st = AFFT_ERR_CUDA;
         }
     }
+    if (st == AFFT_OK && precision == AFFT_F64 && p->d_tw) {
+        // float-float tables for the FP64 kernels' fast path; every specialised axis uses them
+        const int count = (int)tm.size();
+        if (cudaMalloc(&p->d_twdf, (size_t)count * 16) != cudaSuccess) {
+            p->d_twdf = nullptr;
+            st = AFFT_ERR_NOMEM;
+        } else {
+            k_twiddles_df<<<(count + 255) / 256, 256>>>((const double2 *)p->d_tw, (float4 *)p->d_twdf, count);
+            if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) st = AFFT_ERR_CUDA;
+            const char *base = (const char *)p->d_twdf;
+            for (int a = 0; a < 3; ++a) p->ax[a].desc.twdf = base + (size_t)p->ax[a].tw_base * 16;
+            p->ax[2].desc.post_df = base + (size_t)p->post_off * 16;
+        }
+    }
     if (st == AFFT_OK && any_four) {
         const size_t bytes = (size_t)n[0] * n[1] * p->nhp * cplx_size(precision);
         if (cudaMalloc(&p->d_four, bytes) != cudaSuccess) {
@@ -899,9 +926,10 @@ int afft_plan_destroy(afft_plan *p)
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     int st = AFFT_OK;
-    if (p->d_tw || p->d_work || p->d_err || p->d_four) {
+    if (p->d_tw || p->d_work || p->d_err || p->d_four || p->d_twdf) {
         if (cudaDeviceSynchronize() != cudaSuccess) st = AFFT_ERR_CUDA;
         if (p->d_tw) cudaFree(p->d_tw);
+        if (p->d_twdf) cudaFree(p->d_twdf);
         if (p->d_work) cudaFree(p->d_work);
         if (p->d_err) cudaFree(p->d_err);
         if (p->d_four) cudaFree(p->d_four);

@@ -27,6 +27,10 @@ struct StageDesc {
     int tw_off[kMaxPasses];        // first twiddle of each pass (complex entries)
     int ld;                        // r2c/c2r stage: stride between half-spectrum lines, in complex
                                    // elements; 0 means compact (M + 1 for a line of M points)
+    // FP64 plans: the same twiddle tables as float-float values (hi, lo floats),
+    // or null to compute in FP64 (specialised kernels then use float-float)
+    const void *twdf;              // this axis' tables, same offsets as `tw`
+    const void *post_df;           // the r2c/c2r table w_{2M}^k
 };
 
 // Butterflies a thread carries per pass for radix R: at most 16 complex
@@ -72,7 +76,8 @@ enum { KS_STRIDED_FWD = 0, KS_STRIDED_BWD, KS_CONTIG_FWD, KS_CONTIG_BWD, KS_R2C,
 // Pipelined strided kernels (persistent CTAs, double-buffered tiles), indexed
 // by PIPE_*.  Signature: (const V *in, V *out, CUtensorMap map, const V *tw,
 // long long W, long long tiles_per_outer, long long ntiles, unsigned *err,
-// long long Wout, int remap_in, int remap_out); the TMA variants read through
+// long long Wout, int remap_in, int remap_out, const void *twdf) (twdf: the
+// float-float twiddles of an FP64 plan, or null); the TMA variants read through
 // `map`, the cp.async ones through `in`.  Input column c is stored to output
 // column c (remap_in == 0), or, with q = c / remap_in and k = c % remap_in,
 // to q * remap_out + k when k < remap_out and nowhere otherwise (used to move

@@ -10,7 +10,21 @@
 
 namespace afft {
 
-template <typename V> __device__ __forceinline__ V czero() { return cmk<V>(0, 0); }
+// CTA-wide decision after a float-float first pass: keep float-float only if no
+// value of the tile was too large and some value was >= 2^-50 (two votes, so
+// every thread of the CTA must call it).
+__device__ __forceinline__ bool df_tile_ok(const DfFlags &f)
+{
+    const int large = __syncthreads_or(f.large);
+    const int normal = __syncthreads_or(f.normal);
+    return !large && normal;
+}
+
+template <typename V> __device__ __forceinline__ V czero()
+{
+    V v{};
+    return v;
+}
 
 // Shared-memory tile of a strided stage: [n][lines], one 128-byte row per
 // line position (conflict-free for line-fast thread maps).
@@ -36,23 +50,28 @@ template <typename V> struct SmemLines {
     __device__ __forceinline__ void operator()(int l, int p, V v) const { sm[at(l, p)] = v; }
 };
 
+// Global accessors store type V and compute in CT (the same, or float-float
+// for FP64 data): sources convert on load and record out-of-range values in
+// *bad, sinks convert on store.
+
 // Global columns c0 .. c0+lines-1 of a [outer][n][W] slab (strided stage).
-template <typename V> struct GlobalCols {
+template <typename V, typename CT = V> struct GlobalCols {
     const V *base;                 // &x[o][0][c0]
     long long W;
     int valid;                     // columns of the tile inside the array
-    __device__ __forceinline__ V operator()(int l, int p) const
+    DfFlags *bad;
+    __device__ __forceinline__ CT operator()(int l, int p) const
     {
-        return l < valid ? base[(long long)p * W + l] : czero<V>();
+        return l < valid ? Conv<CT, V>::in(base[(long long)p * W + l], bad) : czero<CT>();
     }
 };
-template <typename V> struct GlobalColsOut {
+template <typename V, typename CT = V> struct GlobalColsOut {
     V *base;
     long long W;
     int valid;
-    __device__ __forceinline__ void operator()(int l, int p, V v) const
+    __device__ __forceinline__ void operator()(int l, int p, CT v) const
     {
-        if (l < valid) base[(long long)p * W + l] = v;
+        if (l < valid) base[(long long)p * W + l] = Conv<CT, V>::out(v);
     }
 };
 
@@ -60,34 +79,43 @@ template <typename V> struct GlobalColsOut {
 // every call comes from the thread that owns one column (line-fast maps with a
 // CTA size that is a multiple of the tile width), so the destination column
 // `col` (or -1 for "not stored") is resolved once per tile per thread.
-template <typename V> struct GlobalColRemapOut {
+template <typename V, typename CT = V> struct GlobalColRemapOut {
     V *base;                       // &y[o][0][0]
     long long W;                   // output row pitch
     long long col;                 // this thread's output column, -1 to drop
-    __device__ __forceinline__ void operator()(int, int p, V v) const
+    __device__ __forceinline__ void operator()(int, int p, CT v) const
     {
-        if (col >= 0) base[(long long)p * W + col] = v;
+        if (col >= 0) base[(long long)p * W + col] = Conv<CT, V>::out(v);
     }
 };
 
+// Shared-memory rows holding storage values V, read as compute values CT
+// (the first pass of a float-float tile that a TMA copy brought in as FP64).
+template <typename V, typename CT, int LG> struct SmemRowsConvIn {
+    const V *sm;
+    DfFlags *bad;
+    __device__ __forceinline__ CT operator()(int l, int p) const { return Conv<CT, V>::in(sm[(p << LG) + l], bad); }
+};
+
 // Global contiguous lines b0 .. b0+lines-1 of length n (contiguous stage).
-template <typename V> struct GlobalLines {
+template <typename V, typename CT = V> struct GlobalLines {
     const V *base;                 // &x[b0][0]
     int n;                         // line stride in complex elements
     int valid;
-    __device__ __forceinline__ V operator()(int l, int p) const
+    DfFlags *bad;
+    __device__ __forceinline__ CT operator()(int l, int p) const
     {
-        return l < valid ? base[l * n + p] : czero<V>();
+        return l < valid ? Conv<CT, V>::in(base[l * n + p], bad) : czero<CT>();
     }
 };
-template <typename V> struct GlobalLinesOut {
+template <typename V, typename CT = V> struct GlobalLinesOut {
     V *base;
     int n;
     int valid;
-    typename RealOf<V>::T scale;   // 1 forward, 1/N for the last backward store
-    __device__ __forceinline__ void operator()(int l, int p, V v) const
+    typename RealOf<CT>::T scale;  // 1 forward, 1/N for the last backward store
+    __device__ __forceinline__ void operator()(int l, int p, CT v) const
     {
-        if (l < valid) base[l * n + p] = cscale(v, scale);
+        if (l < valid) base[l * n + p] = Conv<CT, V>::out(cscale(v, scale));
     }
 };
 
@@ -96,25 +124,26 @@ template <typename V> struct GlobalLinesOut {
 //   E[k] = X[k] + conj(X[M-k]),  O[k] = (X[k] - conj(X[M-k])) w_{2M}^{+k},
 // with the imaginary parts of the self-conjugate bins X[0], X[M] dropped.
 // (The factor 1/2 of the textbook identity is folded into the 1/N scale.)
-template <typename V> struct C2RPre {
+template <typename V, typename CT = V> struct C2RPre {
     const V *base;                 // &X[b0][0]
-    const V *post_tw;              // w_{2M}^k forward, k = 0..M
+    const CT *post_tw;             // w_{2M}^k forward, k = 0..M
     int M;
     int ld;                        // line stride (M + 1 compact, more when padded)
     int valid;
-    __device__ __forceinline__ V operator()(int l, int k) const
+    DfFlags *bad;
+    __device__ __forceinline__ CT operator()(int l, int k) const
     {
-        if (l >= valid) return czero<V>();
+        if (l >= valid) return czero<CT>();
         const V *x = base + l * ld;
-        V a = x[k];
-        V b = cconj(x[M - k]);
+        CT a = Conv<CT, V>::in(x[k], bad);
+        CT b = cconj(Conv<CT, V>::in(x[M - k], bad));
         if (k == 0) {
-            a.y = 0;
-            b.y = 0;
+            a.y = typename RealOf<CT>::T();
+            b.y = typename RealOf<CT>::T();
         }
-        const V e = cadd(a, b);
-        const V o = cmulc(csub(a, b), __ldg(post_tw + k));
-        return cmk<V>(e.x - o.y, e.y + o.x);
+        const CT e = cadd(a, b);
+        const CT o = cmulc(csub(a, b), ldgc(post_tw + k));
+        return cmk<CT>(e.x - o.y, e.y + o.x);
     }
 };
 
@@ -135,7 +164,7 @@ template <int S, typename V> struct FourStepSrc {
     {
         if (l >= valid) return czero<V>();
         const V v = base[(long long)p * W + l];
-        const V w = __ldg(wn + p * kb);   // p * kb < n_a n_b = n
+        const V w = ldgc(wn + p * kb);   // p * kb < n_a n_b = n
         return S < 0 ? cmul(v, w) : cmulc(v, w);
     }
 };

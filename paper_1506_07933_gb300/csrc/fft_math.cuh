@@ -11,9 +11,52 @@
 
 namespace afft {
 
+// ------------------------------------------------------- float-float ------
+// FP64 transforms compute in "float-float": a value is hi + lo with two
+// floats (about 48 significant bits), because GB300 executes FP32 about 58x
+// faster than FP64 (measured: FFMA 73.5, DFMA 1.26 TFLOP/s).  Sums use the
+// error-free TwoSum of the hi parts (Knuth), products the FMA-exact residual;
+// lo is renormalised (FastTwoSum) once per radix pass.  Values are not kept
+// normalised between passes: hi + lo stays exact up to the FP32 rounding of the
+// lo accumulation, about 2^-48 relative.
+struct dfl {
+    float hi, lo;
+    __host__ __device__ constexpr dfl() : hi(0.f), lo(0.f) {}
+    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+    // compile-time split of a double constant (no FP64 instruction at run time)
+    __host__ __device__ constexpr explicit dfl(double c) : hi((float)c), lo((float)(c - (double)(float)c)) {}
+};
+__device__ __forceinline__ dfl operator+(dfl a, dfl b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (b.hi - bb);
+    return dfl(s, err + (a.lo + b.lo));
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return dfl(p, e);
+}
+__device__ __forceinline__ dfl renorm(dfl a)
+{
+    const float s = a.hi + a.lo;
+    return dfl(s, a.lo - (s - a.hi));
+}
+
+struct dcx {
+    dfl x, y;
+};
+
 template <typename V> struct RealOf;
 template <> struct RealOf<float2> { using T = float; };
 template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<dcx> { using T = dfl; };
 
 template <typename V>
 __device__ __forceinline__ V cmk(typename RealOf<V>::T x, typename RealOf<V>::T y)
@@ -22,6 +65,11 @@ __device__ __forceinline__ V cmk(typename RealOf<V>::T x, typename RealOf<V>::T 
     v.x = x;
     v.y = y;
     return v;
+}
+// T(c) of a double constant for any real type (split at compile time for dfl)
+template <typename V> __device__ __forceinline__ typename RealOf<V>::T rconst(double c)
+{
+    return typename RealOf<V>::T(c);
 }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
@@ -186,5 +234,90 @@ template <int S, typename V> struct Dft<5, S, V> {
     }
 };
 
+
+// ------------------------------------------- float-float conversions -----
+
+// Split of a double into float-float using integer operations only (no FP64
+// instruction): hi takes the top 24 significand bits, lo the remaining 29 bits
+// rounded to 24 (exact to 2^-48 relative).  Flags for the tile-wide decision:
+// `large` for |x| >= 2^101, inf or nan (an FFT stage grows values by up to n <=
+// 2^12, which must stay below float's 2^128); `normal` for |x| >= 2^-50.
+// Values below 2^-74 keep only hi (below 2^-126: zero); that is negligible when
+// the tile holds some value >= 2^-50, which the caller checks.
+struct DfFlags {
+    bool large = false;
+    bool normal = false;
+};
+__device__ __forceinline__ dfl dfl_from_double(double x, DfFlags &f)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned e = (unsigned)(u >> 52) & 0x7ffu;
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    const unsigned sgn = (unsigned)(u >> 63);
+    if (e >= 1124u) {  // |x| >= 2^101, inf, nan
+        f.large = true;
+        return dfl(0.f, 0.f);
+    }
+    if (e >= 973u) f.normal = true;
+    if (e < 897u) return dfl(0.f, 0.f);   // below float's normal range
+    const float hi = __uint_as_float((sgn << 31) | ((e - 896u) << 23) | (unsigned)(m >> 29));
+    if (e < 949u) return dfl(hi, 0.f);
+    const int r = (int)(m & 0x1FFFFFFFull);
+    const float lo = (float)(sgn ? -r : r) * __uint_as_float((e - 948u) << 23);
+    return dfl(hi, lo);
+}
+
+// Exact float -> double by bit placement (normal floats; zero and subnormals
+// give zero), then one FP64 add for hi + lo.
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    return e == 0 ? 0.0 : __longlong_as_double((long long)d);
+}
+__device__ __forceinline__ double dfl_to_double(dfl a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+
+// Renormalises the float-float parts of a complex value (identity otherwise).
+template <typename V> __device__ __forceinline__ V cnorm(V v) { return v; }
+template <> __device__ __forceinline__ dcx cnorm<dcx>(dcx v)
+{
+    dcx r;
+    r.x = renorm(v.x);
+    r.y = renorm(v.y);
+    return r;
+}
+
+// Read-only cached load of one complex value.
+template <typename V> __device__ __forceinline__ V ldgc(const V *p) { return __ldg(p); }
+template <> __device__ __forceinline__ dcx ldgc<dcx>(const dcx *p)
+{
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    dcx r;
+    r.x = dfl(q.x, q.y);
+    r.y = dfl(q.z, q.w);
+    return r;
+}
+
+// Storage <-> compute conversions (identity unless double2 <-> dcx).
+template <typename CT, typename V> struct Conv {
+    static __device__ __forceinline__ CT in(V v, DfFlags *) { return v; }
+    static __device__ __forceinline__ V out(CT v) { return v; }
+};
+template <> struct Conv<dcx, double2> {
+    static __device__ __forceinline__ dcx in(double2 v, DfFlags *f)
+    {
+        dcx r;
+        r.x = dfl_from_double(v.x, *f);
+        r.y = dfl_from_double(v.y, *f);
+        return r;
+    }
+    static __device__ __forceinline__ double2 out(dcx v)
+    {
+        return make_double2(dfl_to_double(v.x), dfl_to_double(v.y));
+    }
+};
 
 }  // namespace afft

@@ -219,7 +219,7 @@ __device__ __forceinline__ void pair_pass(const float2 *src, const float2 *__res
                 const float2 *t = tw + k * (R - 1);
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const float2 w = __ldg(t + r - 1);
+                    const float2 w = ldgc(t + r - 1);
                     lo[r] = ctw<S>(lo[r], w);
                     hi[r] = ctw<S>(hi[r], w);
                 }
@@ -233,16 +233,17 @@ __device__ __forceinline__ void pair_pass(const float2 *src, const float2 *__res
     }
 }
 
-// The stage's global output for both pass kinds, resolved per thread per tile.
-template <typename V> struct TileOut {
-    GlobalColRemapOut<V> single;   // one column per thread
-    PairGlobalOut pair;            // two columns per thread (float2 only)
+// The stage's global output for both pass kinds, resolved per thread per tile
+// (stored as V, computed as CT).
+template <typename V, typename CT = V> struct TileOut {
+    GlobalColRemapOut<V, CT> single;  // one column per thread
+    PairGlobalOut pair;               // two columns per thread (float2 only)
 };
 
 // Passes Seq<R, Rest...>: pass number Q reads buffer X (Q even) or C (Q odd)
 // and writes the other one; the last pass writes the stage's output.
-template <class Sh, int S, int N, int Ns, int TwOff, int Q, typename V, int R, int... Rest>
-__device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V *tw, const TileOut<V> &out)
+template <class Sh, int S, int N, int Ns, int TwOff, int Q, typename V, class Out, int R, int... Rest>
+__device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V *tw, const Out &out)
 {
     constexpr bool Last = sizeof...(Rest) == 0;
     constexpr int LG = Sh::lg, NT = Sh::threads;
@@ -267,13 +268,30 @@ __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V
     }
 }
 
+// FP64 tile in float-float: the first pass converts the FP64 tile X (as the
+// TMA copy left it) into float-float values in C and votes on range; the
+// remaining passes continue in float-float (Q = 1: C -> X -> ...).  Returns
+// false, with X untouched, when some value was out of float-float range.
+template <class Sh, int S, int N, class Out, int R0, int... Rest>
+__device__ __forceinline__ bool pipe_df(Seq<R0, Rest...>, double2 *X, double2 *C, const dcx *tw, const Out &out)
+{
+    constexpr int LG = Sh::lg, NT = Sh::threads;
+    DfFlags bad;
+    const SmemRowsConvIn<double2, dcx, LG> src{X, &bad};
+    radix_pass<R0, S, false, NT>(N, 1, tw, Sh::lines, MapLineFastC<LG>{}, src,
+                                 SmemRowsC<dcx, LG>{reinterpret_cast<dcx *>(C)});
+    if (!df_tile_ok(bad)) return false;
+    pipe_passes<Sh, S, N, R0, 0, 1>(Seq<Rest...>{}, reinterpret_cast<dcx *>(X), reinterpret_cast<dcx *>(C), tw, out);
+    return true;
+}
+
 // ---------------------------------------------------------------- kernel ---
 
 template <class P, int S, typename V, bool TMA>
 __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     k_strided_pipe(const V *__restrict__ in, V *out, const __grid_constant__ CUtensorMap tmap,
                    const V *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
-                   unsigned *err, long long Wout, int remap_in, int remap_out)
+                   unsigned *err, long long Wout, int remap_in, int remap_out, const void *twdf)
 {
     using Sh = PipeShape<P, V>;
     constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
@@ -355,7 +373,15 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
                              (reinterpret_cast<unsigned long long>(base) & 15) == 0;
             to.pair = PairGlobalOut{base, Wout, a, bcol, vec};
         }
-        pipe_passes<Sh, S, N, 1, 0, 0>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to);
+        bool done = false;
+        if constexpr (std::is_same<V, double2>::value && P::npass >= 2) {
+            if (twdf) {
+                TileOut<V, dcx> tdf;
+                tdf.single = GlobalColRemapOut<V, dcx>{to.single.base, to.single.W, to.single.col};
+                done = pipe_df<Sh, S, N>(typename P::seq{}, buf0 + b * TILE, scratch, (const dcx *)twdf, tdf);
+            }
+        }
+        if (!done) pipe_passes<Sh, S, N, 1, 0, 0>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to);
         if (tn >= ntiles) break;
         t = tn;
     }

@@ -26,6 +26,8 @@
 //    at run time by its radix.
 #pragma once
 
+#include <type_traits>
+
 #include "afft_internal.h"
 #include "fft_access.cuh"
 
@@ -80,7 +82,7 @@ __device__ __forceinline__ void radix_pass(int n, int Ns, const V *__restrict__ 
             if (Ns > 1) {
                 const V *t = tw + (j % Ns) * (R - 1);
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[b][r] = ctw<S>(v[b][r], __ldg(t + r - 1));
+                for (int r = 1; r < R; ++r) v[b][r] = ctw<S>(v[b][r], ldgc(t + r - 1));
             }
             Dft<R, S, V>::run(v[b]);
         }
@@ -93,7 +95,7 @@ __device__ __forceinline__ void radix_pass(int n, int Ns, const V *__restrict__ 
             const int k = j % Ns;
             const int o = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst(lb[b], o + r * Ns, v[b][r]);
+            for (int r = 0; r < R; ++r) dst(lb[b], o + r * Ns, cnorm(v[b][r]));
         }
     }
 }
@@ -147,6 +149,34 @@ __device__ __forceinline__ void run_plan(const V *tw, int lines, const Map &map,
         run_passes<S, true, LastToSmem, P::n, 1, 0>(typename P::seq{}, tw, lines, map, src, sm, dst);
     }
 }
+
+// Float-float stage for FP64 data (see dfl): the first pass converts the
+// FP64 input on load and records any value outside float-float range; a
+// CTA-wide vote then either continues in float-float or reports failure, in
+// which case the caller redoes the tile in FP64 (the first pass wrote only
+// shared memory, so the input is untouched).  Plans with one pass are not
+// eligible (their only pass writes the output).
+template <class P, int S, bool LastToSmem, typename CT, class Map, class Src, class Sm, class Dst, int R0,
+          int... Rest>
+__device__ __forceinline__ bool df_stage_impl(Seq<R0, Rest...>, const CT *tw, int lines, const Map &map,
+                                              const Src &src, const Sm &sm, const Dst &dst, const DfFlags &bad)
+{
+    radix_pass<R0, S, false>(P::n, 1, tw, lines, map, src, sm);
+    if (!df_tile_ok(bad)) return false;
+    run_passes<S, false, LastToSmem, P::n, R0, 0>(Seq<Rest...>{}, tw, lines, map, sm, sm, dst);
+    return true;
+}
+template <class P, int S, bool LastToSmem, typename CT, class Map, class Src, class Sm, class Dst>
+__device__ __forceinline__ bool df_stage(const CT *tw, int lines, const Map &map, const Src &src, const Sm &sm,
+                                         const Dst &dst, const DfFlags &bad)
+{
+    return df_stage_impl<P, S, LastToSmem>(typename P::seq{}, tw, lines, map, src, sm, dst, bad);
+}
+
+// Specialised FP64 kernels with at least two passes compute in float-float.
+template <class F, typename V> struct UseDf {
+    static constexpr bool value = !F::generic && std::is_same<V, double2>::value && F::plan::npass >= 2;
+};
 
 // ------------------------------------------------- generic pass sequence ----
 // One non-inlined function per (radix, direction, layout): the tile lives in
@@ -255,6 +285,15 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     if constexpr (F::generic) {
         run_generic<S, true, false>(d, tw, sm, lines, log2_lines, map, src, dst);
     } else {
+        if constexpr (UseDf<F, V>::value) {
+            if (d.twdf) {
+                DfFlags bad;
+                const GlobalCols<V, dcx> sdf{in + off, W, valid, &bad};
+                const GlobalColsOut<V, dcx> ddf{out + off, W, valid};
+                const SmemRows<dcx> tdf{reinterpret_cast<dcx *>(sm), log2_lines};
+                if (df_stage<typename F::plan, S, false>((const dcx *)d.twdf, lines, map, sdf, tdf, ddf, bad)) return;
+            }
+        }
         const SmemRows<V> tile{sm, log2_lines};
         run_plan<typename F::plan, S, false>(tw, lines, map, src, tile, dst);
     }
@@ -277,8 +316,38 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     if constexpr (F::generic) {
         run_generic<S, false, false>(d, tw, sm, lines, 0, map, src, dst);
     } else {
+        if constexpr (UseDf<F, V>::value) {
+            if (d.twdf) {
+                DfFlags bad;
+                const GlobalLines<V, dcx> sdf{in + b0 * n, n, valid, &bad};
+                const GlobalLinesOut<V, dcx> ddf{out + b0 * n, n, valid, dfl(scale)};
+                const SmemLines<dcx> tdf{reinterpret_cast<dcx *>(sm), n};
+                if (df_stage<typename F::plan, S, false>((const dcx *)d.twdf, lines, map, sdf, tdf, ddf, bad)) return;
+            }
+        }
         const SmemLines<V> tile{sm, n};
         run_plan<typename F::plan, S, false>(tw, lines, map, src, tile, dst);
+    }
+}
+
+// r2c post-processing of the DFT_M lines in shared memory into M+1 bins per
+// line (compute type CT, stored as V):
+//   X[k] = E[k] + w_{2M}^k O[k],  E = (Z[k] + conj Z[M-k]) / 2,
+//   O = (Z[k] - conj Z[M-k]) / (2i),  Z[M] = Z[0].
+template <typename V, typename CT, class Tile>
+__device__ __forceinline__ void r2c_post(const Tile &tile, V *o, const CT *post_tw, int M, int ld, int valid)
+{
+    using T = typename RealOf<CT>::T;
+    const int per = M + 1;
+    for (int idx = threadIdx.x; idx < valid * per; idx += blockDim.x) {
+        const int l = idx / per;
+        const int k = idx - l * per;
+        const CT zk = tile(l, k == M ? 0 : k);
+        const CT zm = cconj(tile(l, k == 0 ? 0 : M - k));
+        const CT e = cscale(cadd(zk, zm), T(0.5));
+        const CT dd = csub(zk, zm);
+        const CT od = cmk<CT>(T(0.5) * dd.y, T(-0.5) * dd.x);  // (zk - zm) / (2i)
+        o[l * ld + k] = Conv<CT, V>::out(cnorm(cadd(e, cmul(od, ldgc(post_tw + k)))));
     }
 }
 
@@ -301,22 +370,25 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     const GlobalLines<V> src{reinterpret_cast<const V *>(in) + b0 * M, M, valid};
     const SmemLines<V> tile{sm, M};
     const MapButterflyFast map{};
+    const int ld = d.ld > 0 ? d.ld : M + 1;  // output line stride (padded layouts leave a gap)
+    V *o = out + b0 * ld;
+    if constexpr (UseDf<F, V>::value) {
+        if (d.twdf) {
+            DfFlags bad;
+            const GlobalLines<V, dcx> sdf{reinterpret_cast<const V *>(in) + b0 * M, M, valid, &bad};
+            const SmemLines<dcx> tdf{reinterpret_cast<dcx *>(sm), M};
+            if (df_stage<typename F::plan, -1, true>((const dcx *)d.twdf, lines, map, sdf, tdf, tdf, bad)) {
+                __syncthreads();
+                r2c_post<V, dcx>(tdf, o, (const dcx *)d.post_df, M, ld, valid);
+                return;
+            }
+        }
+    }
     if constexpr (F::generic) run_generic<-1, false, true>(d, tw, sm, lines, 0, map, src, tile);
     else run_plan<typename F::plan, -1, true>(tw, lines, map, src, tile, tile);
     __syncthreads();
-    const int ld = d.ld > 0 ? d.ld : M + 1;  // output line stride (padded layouts leave a gap)
-    V *o = out + b0 * ld;
-    const int per = M + 1;
-    for (int idx = threadIdx.x; idx < valid * per; idx += blockDim.x) {
-        const int l = idx / per;
-        const int k = idx - l * per;
-        const V zk = tile(l, k == M ? 0 : k);
-        const V zm = cconj(tile(l, k == 0 ? 0 : M - k));
-        const V e = cscale(cadd(zk, zm), T(0.5));
-        const V dd = csub(zk, zm);
-        const V od = cmk<V>(T(0.5) * dd.y, T(-0.5) * dd.x);  // (zk - zm) / (2i)
-        o[l * ld + k] = cadd(e, cmul(od, __ldg(post_tw + k)));
-    }
+    r2c_post<V, V>(tile, o, post_tw, M, ld, valid);
+    (void)sizeof(T);
 }
 
 // Contiguous axis, M+1 bins -> real line of 2M points (backward, last stage):
@@ -340,6 +412,15 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     if constexpr (F::generic) {
         run_generic<+1, false, false>(d, tw, sm, lines, 0, map, src, dst);
     } else {
+        if constexpr (UseDf<F, V>::value) {
+            if (d.twdf) {
+                DfFlags bad;
+                const C2RPre<V, dcx> sdf{in + b0 * ld, (const dcx *)d.post_df, M, ld, valid, &bad};
+                const GlobalLinesOut<V, dcx> ddf{reinterpret_cast<V *>(out) + b0 * M, M, valid, dfl(scale)};
+                const SmemLines<dcx> tdf{reinterpret_cast<dcx *>(sm), M};
+                if (df_stage<typename F::plan, +1, false>((const dcx *)d.twdf, lines, map, sdf, tdf, ddf, bad)) return;
+            }
+        }
         const SmemLines<V> tile{sm, M};
         run_plan<typename F::plan, +1, false>(tw, lines, map, src, tile, dst);
     }

@@ -438,3 +438,37 @@ def test_four_step_long_lines_r2c(shape, prec):
     H = ref.astype(CDT[prec])
     report("four-step c2r %s %s" % (shape, prec), oracle.rel_l2(gpu_c2r(H, shape, prec), oracle.c2r(H, shape[2])),
            TOL[prec])
+
+
+@pytest.mark.parametrize("scale", [1e-300, 1e-30, 1e30, 1e200])
+@pytest.mark.parametrize("kind", ["c2c", "r2c"])
+def test_fp64_extreme_magnitudes(scale, kind):
+    """FP64 kernels compute in float-float when every value of a tile lies in its range
+    (2^-74 .. 2^127) and redo the tile in FP64 otherwise; results stay within 1e-12 for inputs
+    far outside float range, including a field where only some tiles are extreme."""
+    shape = (64, 48, 96)
+    if kind == "c2c":
+        x = synth.uniform_complex(shape, 61) * scale
+    else:
+        x = synth.uniform_real(shape, 61) * scale
+    x[:4] /= scale   # a few planes of ordinary magnitude: mixed tiles
+    if kind == "c2c":
+        report("c2c f64 x %g" % scale, oracle.rel_l2(gpu_c2c(x, "f64"), oracle.c2c(x)), TOL["f64"])
+        report("c2c bwd f64 x %g" % scale, oracle.rel_l2(gpu_c2c(x, "f64", +1), oracle.c2c(x, +1)), TOL["f64"])
+    else:
+        ref = oracle.r2c(x)
+        report("r2c f64 x %g" % scale, oracle.rel_l2(gpu_r2c(x, "f64"), ref), TOL["f64"])
+        report("c2r f64 x %g" % scale, oracle.rel_l2(gpu_c2r(ref, shape, "f64"), oracle.c2r(ref, shape[2])),
+               TOL["f64"])
+
+
+def test_fp64_tiny_values_mixed_with_ordinary_ones():
+    """Values below float-float precision range inside tiles that also hold ordinary values stay on
+    the fast path (their contribution is negligible); accuracy must hold."""
+    shape = (64, 48, 96)
+    x = synth.uniform_complex(shape, 62)
+    x[:, :, ::3] *= 1e-30
+    x[:, ::5, :] *= 1e-200
+    report("c2c f64 tiny mixed", oracle.rel_l2(gpu_c2c(x, "f64"), oracle.c2c(x)), TOL["f64"])
+    r = x.real.copy()
+    report("r2c f64 tiny mixed", oracle.rel_l2(gpu_r2c(r, "f64"), oracle.r2c(r)), TOL["f64"])
