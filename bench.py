@@ -38,8 +38,8 @@ WORKLOAD = ("r2c forward + c2r backward, 512x512x512 %s random-mode field (64 mo
             "+1e-3 noise)")
 STAGE_NAMES_FWD = ["r2c z-stage (N2)", "strided y-stage (N1)", "strided x-stage (N0)"]
 STAGE_NAMES_BWD = ["strided x-stage (N0)", "strided y-stage (N1)", "c2r z-stage (N2)"]
-KERNEL_NAMES_FWD = ["k_r2c", "k_strided", "k_strided"]
-KERNEL_NAMES_BWD = ["k_strided", "k_strided", "k_c2r"]
+KERNEL_NAMES_FWD = ["k_r2c", "k_strided_pipe", "k_strided_pipe"]
+KERNEL_NAMES_BWD = ["k_strided_pipe", "k_strided_pipe", "k_c2r"]
 
 
 def peaks():
