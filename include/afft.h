@@ -97,6 +97,16 @@ enum {
 int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precision);
 
 /*
+ * A plan for `batch` independent transforms of the same size stored back to
+ * back ([batch][n0][n1][n2], and [batch][n0][n1][n2/2+1] for r2c spectra).
+ * The stages run over all of them at once (the batch simply adds lines to
+ * every stage, as the paper's batched 1-D FFTs do within one rank).
+ * afft_plan_create(out, n, kind, precision) is batch = 1.  batch < 1 returns
+ * AFFT_ERR_SIZE; input/output byte counts below include the batch.
+ */
+int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch, int kind, int precision);
+
+/*
  * Forward transform (Algorithm 1, left column): 1-D FFTs along N2, then N1,
  * then N0, unscaled.  C2C: in, out complex [n0][n1][n2].  R2C: in real
  * [n0][n1][n2], out complex [n0][n1][n2/2+1].  Device pointers; stream is a
@@ -163,6 +173,45 @@ int afft_plan_set_l2_chunk(afft_plan *p, size_t bytes);
 
 /* Slab size in use (0 when the stages run unfused). */
 size_t afft_plan_l2_chunk(const afft_plan *p);
+
+/*
+ * Autotuner (the counterpart of the MEASURE planner flag AccFFT passes to FFTW
+ * and cuFFT, Section 3 "Implementation Details").  Times forward + backward
+ * round trips of this plan on temporary buffers (allocated and freed here,
+ * filled by afft_fill_uniform) for: the points per CTA of the contiguous
+ * stage (1024 .. 8192), pipelined or plain kernels for each strided stage,
+ * and, for arrays beyond 192 MB, the L2 slab size (0, 32, 64 MB); keeps the
+ * fastest choice of each, in that order.  Results do not depend on the choice
+ * beyond rounding.  Synchronises the stream.  AFFT_ERR_NOMEM if the temporary
+ * buffers do not fit.
+ */
+int afft_plan_tune(afft_plan *p, void *cuda_stream);
+
+/*
+ * Writes a one-line JSON description of the plan's configuration (radix
+ * sequences per axis, kernel families, four-step splits, pipelined stages,
+ * lines per CTA, padded row pitch, L2 slab) into buf (NUL-terminated).
+ * AFFT_ERR_SIZE if len is too small.
+ */
+int afft_plan_describe(const afft_plan *p, char *buf, size_t len);
+
+/*
+ * Multi-plan executor: several plans (for example one batched plan per
+ * distinct size of a set of uneven transforms) run as one CUDA graph.  The
+ * first execute with a given direction and set of buffers captures, on a
+ * private stream, one branch per plan (forked from a common event, so the
+ * groups overlap on the GPU) and instantiates the graph; later executes with
+ * the same buffers replay it with one cudaGraphLaunch on `cuda_stream`.  Up to
+ * 8 captured graphs are kept (least recently used evicted).  The plans stay
+ * owned by the caller and must outlive the executor; while captured graphs
+ * exist, plans must not be reconfigured (tune, L2 slab, timing).  in[i] and
+ * out[i] are device buffers for plans[i] (forward: its spatial input and
+ * spectral output; backward: the reverse).
+ */
+typedef struct afft_multi afft_multi;
+int afft_multi_create(afft_multi **out, int nplans, afft_plan *const *plans);
+int afft_multi_execute(afft_multi *m, int backward, const void *const *in, void *const *out, void *cuda_stream);
+int afft_multi_destroy(afft_multi *m);
 
 /* Number of kernel launches one execute_forward / execute_backward makes. */
 int afft_plan_launches(const afft_plan *p, int backward);

@@ -40,6 +40,8 @@ EXPORTS = [
     "afft_plan_launches", "afft_status_string", "afft_fill_uniform",
     "afft_plan_timing_begin", "afft_plan_timing_end", "afft_c2r_noalloc",
     "afft_plan_device_status", "afft_plan_set_l2_chunk", "afft_plan_l2_chunk",
+    "afft_plan_create_batched", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
+    "afft_multi_execute", "afft_multi_destroy",
 ]
 
 _lib = None
@@ -62,6 +64,12 @@ def load(path: str = None):
     lib = ctypes.CDLL(path)
     vp, i64p, c_int, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_size_t
     lib.afft_plan_create.argtypes = [ctypes.POINTER(vp), i64p, c_int, c_int]
+    lib.afft_plan_create_batched.argtypes = [ctypes.POINTER(vp), i64p, ctypes.c_int64, c_int, c_int]
+    lib.afft_plan_tune.argtypes = [vp, vp]
+    lib.afft_plan_describe.argtypes = [vp, ctypes.c_char_p, sz]
+    lib.afft_multi_create.argtypes = [ctypes.POINTER(vp), c_int, ctypes.POINTER(vp)]
+    lib.afft_multi_execute.argtypes = [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.afft_multi_destroy.argtypes = [vp]
     lib.afft_execute_forward.argtypes = [vp, vp, vp, vp]
     lib.afft_execute_backward.argtypes = [vp, vp, vp, vp]
     lib.afft_execute_forward_host.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -81,11 +89,12 @@ def load(path: str = None):
     lib.afft_plan_set_l2_chunk.argtypes = [vp, sz]
     lib.afft_plan_l2_chunk.argtypes = [vp]
     lib.afft_plan_l2_chunk.restype = sz
-    for f in ("afft_plan_create", "afft_execute_forward", "afft_execute_backward",
+    for f in ("afft_plan_create", "afft_plan_create_batched", "afft_execute_forward", "afft_execute_backward",
               "afft_execute_forward_host", "afft_execute_backward_host", "afft_plan_destroy",
               "afft_plan_launches", "afft_fill_uniform", "afft_plan_timing_begin",
               "afft_plan_timing_end", "afft_c2r_noalloc", "afft_plan_device_status",
-              "afft_plan_set_l2_chunk"):
+              "afft_plan_set_l2_chunk", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
+              "afft_multi_execute", "afft_multi_destroy"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -112,6 +121,14 @@ def afft_plan_create(shape, kind: int, precision: int) -> ctypes.c_void_p:
     n = (ctypes.c_int64 * 3)(*[int(s) for s in shape])
     p = ctypes.c_void_p()
     _check(load().afft_plan_create(ctypes.byref(p), n, int(kind), int(precision)), "afft_plan_create")
+    return p
+
+
+def afft_plan_create_batched(shape, batch: int, kind: int, precision: int) -> ctypes.c_void_p:
+    n = (ctypes.c_int64 * 3)(*[int(s) for s in shape])
+    p = ctypes.c_void_p()
+    _check(load().afft_plan_create_batched(ctypes.byref(p), n, int(batch), int(kind), int(precision)),
+           "afft_plan_create_batched")
     return p
 
 
@@ -164,12 +181,16 @@ class Plan:
     Calls are asynchronous on the current (or given) stream.
     """
 
-    def __init__(self, shape, kind="c2c", precision="f32"):
+    def __init__(self, shape, kind="c2c", precision="f32", batch=None):
         self.shape = tuple(int(s) for s in shape)
         self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.device = torch.device("cuda", torch.cuda.current_device())
-        self._p = afft_plan_create(self.shape, self.kind, self.precision)
+        self.batch = batch
+        if batch is None:
+            self._p = afft_plan_create(self.shape, self.kind, self.precision)
+        else:
+            self._p = afft_plan_create_batched(self.shape, int(batch), self.kind, self.precision)
         lib = load()
         self.workspace_bytes = lib.afft_plan_workspace_bytes(self._p)
         self.input_bytes = lib.afft_plan_input_bytes(self._p)
@@ -178,12 +199,13 @@ class Plan:
     # shapes / dtypes of the forward input and output
     @property
     def spatial_shape(self):
-        return self.shape
+        return self.shape if self.batch is None else (self.batch,) + self.shape
 
     @property
     def spectral_shape(self):
         n0, n1, n2 = self.shape
-        return (n0, n1, n2 // 2 + 1) if self.kind == R2C else self.shape
+        s = (n0, n1, n2 // 2 + 1) if self.kind == R2C else self.shape
+        return s if self.batch is None else (self.batch,) + s
 
     @property
     def spatial_dtype(self):
@@ -254,6 +276,16 @@ class Plan:
     def l2_chunk(self) -> int:
         return int(load().afft_plan_l2_chunk(self._p))
 
+    def tune(self, stream=None) -> None:
+        """Autotune the launch configuration on temporary buffers (synchronises)."""
+        _check(load().afft_plan_tune(self._p, _stream_handle(stream)), "afft_plan_tune")
+
+    def describe(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(1024)
+        _check(load().afft_plan_describe(self._p, buf, len(buf)), "afft_plan_describe")
+        return json.loads(buf.value.decode())
+
     def device_status(self) -> int:
         """Synchronises; returns 0, or 11 (AFFT_ERR_TIMEOUT) if a bounded wait ran out since the last call."""
         return int(load().afft_plan_device_status(self._p))
@@ -287,6 +319,48 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Multi:
+    """Several plans run as one captured CUDA graph (see afft_multi_* in include/afft.h)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._p.value for p in self.plans])
+        self._m = ctypes.c_void_p()
+        _check(load().afft_multi_create(ctypes.byref(self._m), len(self.plans), arr), "afft_multi_create")
+
+    def _run(self, backward, ins, outs, stream):
+        if len(ins) != len(self.plans) or len(outs) != len(self.plans):
+            raise ValueError("one input and one output per plan")
+        for p, a, b in zip(self.plans, ins, outs):
+            if backward:
+                p._check_tensor(a, p.spectral_shape, p.spectral_dtype, "input")
+                p._check_tensor(b, p.spatial_shape, p.spatial_dtype, "output")
+            else:
+                p._check_tensor(a, p.spatial_shape, p.spatial_dtype, "input")
+                p._check_tensor(b, p.spectral_shape, p.spectral_dtype, "output")
+        ia = (ctypes.c_void_p * len(ins))(*[t.data_ptr() for t in ins])
+        oa = (ctypes.c_void_p * len(outs))(*[t.data_ptr() for t in outs])
+        _check(load().afft_multi_execute(self._m, int(backward), ia, oa, _stream_handle(stream)),
+               "afft_multi_execute")
+
+    def forward(self, ins, outs, stream=None):
+        self._run(0, ins, outs, stream)
+
+    def backward(self, ins, outs, stream=None):
+        self._run(1, ins, outs, stream)
+
+    def close(self):
+        if getattr(self, "_m", None) and self._m.value:
+            _check(load().afft_multi_destroy(self._m), "afft_multi_destroy")
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fill_uniform(t: torch.Tensor, seed: int, stream=None) -> torch.Tensor:

@@ -8,6 +8,7 @@
 // N2 with the 1/N of Section 2, footnote 2 folded into the last store.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -25,7 +26,8 @@ struct AxisPlan {
     const KernelSet *ks;   // kernels for this line length (specialised or generic)
     int tw_base;           // first twiddle of this axis in the plan's table; desc.tw_off is relative
     // pipelined strided kernel (persistent CTAs) when the family has one
-    bool pipe;
+    bool pipe_avail;       // the family has it and it fits this device
+    bool pipe;             // in use (the autotuner may switch it off)
     int pipe_slots;        // CTAs resident at once (SMs x CTAs per SM): the persistent grid's cap
 };
 
@@ -41,6 +43,7 @@ struct FourStep {
 
 struct afft_plan {
     int64_t n[3];
+    int64_t batch;         // transforms per execute, stored back to back
     int kind;
     int precision;
     int64_t nh;            // last-axis length of the complex array: n2 (C2C) or n2/2+1 (R2C)
@@ -63,6 +66,7 @@ struct afft_plan {
     // the N1 stage of slab c on a second stream while the N2 stage of slab c+1 runs
     FourStep four[3];      // per axis
     void *d_four;          // four-step intermediate: n0*n1*nhp complex
+    int contig_target;     // points per CTA of the contiguous stage (0: default)
     size_t chunk_bytes;    // requested slab size (0: off)
     int chunk_planes;      // planes per slab; 0 when the stages run unfused
     cudaStream_t aux;
@@ -195,11 +199,12 @@ bool shape_strided(const StageDesc &d, long long outer, long long W, size_t elem
     }
 }
 
-// Contiguous stage: whole lines, about `target` complex points per CTA.
+// Contiguous stage: whole lines, about `target` complex points per CTA
+// (0: 4096 for complex64, 2048 for complex128; the autotuner may pick others).
 bool shape_contig(const StageDesc &d, long long nlines, size_t elem, int max_threads, size_t max_smem,
-                  Launch &L)
+                  Launch &L, int target = 0)
 {
-    const int target = elem == 8 ? 4096 : 2048;
+    if (target <= 0) target = elem == 8 ? 4096 : 2048;
     int lines = std::max(1, target / std::max(1, d.n));
     lines = (int)std::min<long long>(lines, std::max(1LL, nlines));
     const int row = (int)(128 / elem);
@@ -309,7 +314,7 @@ int plan_shapes(afft_plan *p)
     if (max_smem <= 0) max_smem = 48 * 1024;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh;
+    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh, B = p->batch;
     // strided stages (and the first half of a four-step contiguous axis): persistent
     // double-buffered kernels where the family has them
     for (int a = 0; a < 3; ++a) {
@@ -327,6 +332,7 @@ int plan_shapes(afft_plan *p)
                                                           ks->pipe_smem) != cudaSuccess || per_sm < 1)
             continue;
         ap.pipe_slots = sms * per_sm;
+        ap.pipe_avail = true;
         ap.pipe = true;
     }
     // FP32 r2c with an odd half-spectrum width: rows of nh complex64 are not 16-byte aligned,
@@ -344,13 +350,13 @@ int plan_shapes(afft_plan *p)
     AxisPlan &z = p->ax[2], &y = p->ax[1], &x = p->ax[0];
     // width of each axis' lines (W of its [outer][n][W] view); a four-step axis runs
     // its first half with W * n_a
-    const long long outer[3] = {1, n0, n0 * n1};
+    const long long outer[3] = {B, B * n0, B * n0 * n1};
     const long long width[3] = {n1 * nh, nhp, 1};
     for (int a = 0; a < 3; ++a) {
         const FourStep &f = p->four[a];
         AxisPlan &ap = p->ax[a];
         bool ok;
-        if (a == 2 && !f.on) ok = shape_contig(z.desc, n0 * n1, elem, z.ks->max_threads, budget(z), z.launch);
+        if (a == 2 && !f.on) ok = shape_contig(z.desc, B * n0 * n1, elem, z.ks->max_threads, budget(z), z.launch);
         else ok = shape_strided(ap.desc, outer[a], width[a] * (f.on ? f.na : 1), elem, ap.ks->max_threads,
                                 budget(ap), ap.launch);
         if (!ok) return AFFT_ERR_UNSUPPORTED;
@@ -562,7 +568,8 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
-    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, nhp = p->nhp;
+    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, nhp = p->nhp, B = p->batch;
+    const long long P0 = B * n0;          // planes of all transforms of the batch
     // padded R2C: N2 and N1 stages in the workspace, N0 stage converts to the compact `out`
     V *o = (V *)out;
     V *w = nhp != nh ? (V *)p->d_work : o;
@@ -584,12 +591,12 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
     mark(p, 0, s);
     const int K = p->chunk_planes;
     if (K > 0) {
-        const long long C = (n0 + K - 1) / K;
+        const long long C = (P0 + K - 1) / K;
         cudaEvent_t *ev = p->chunk_ev.data();
         if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess) return AFFT_ERR_CUDA;
         if ((e = cudaStreamWaitEvent(p->aux, ev[0], 0)) != cudaSuccess) return AFFT_ERR_CUDA;
         for (long long c = 0; c < C && e == cudaSuccess; ++c) {
-            const long long p0 = c * K, np = std::min<long long>(K, n0 - p0);
+            const long long p0 = c * K, np = std::min<long long>(K, P0 - p0);
             if (c >= 2) e = cudaStreamWaitEvent(s, ev[1 + 2 * (c - 2) + 1], 0);
             if (e == cudaSuccess) e = zstage(p0, np, s);
             if (e == cudaSuccess) e = cudaEventRecord(ev[1 + 2 * c], s);
@@ -602,18 +609,18 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
         mark(p, 1, s);
         mark(p, 2, s);
     } else {
-        if (zstage(0, n0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        if (zstage(0, P0, s) != cudaSuccess) return AFFT_ERR_CUDA;
         mark(p, 1, s);
-        if (ystage(0, n0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        if (ystage(0, P0, s) != cudaSuccess) return AFFT_ERR_CUDA;
         mark(p, 2, s);
     }
     if (n0 > 1) {
         const Remap rm = nhp != nh ? Remap{n1 * nh, (int)nhp, (int)nh} : Remap{0, 0, 0};
-        if (axis_stage<V>(p, 0, w, o, 1, n1 * nhp, 0, 1.0, s, rm) != cudaSuccess) return AFFT_ERR_CUDA;
+        if (axis_stage<V>(p, 0, w, o, B, n1 * nhp, 0, 1.0, s, rm) != cudaSuccess) return AFFT_ERR_CUDA;
     } else if (w != o) {
-        // one plane: the compact output is the padded workspace without its pad column
-        if (cudaMemcpy2DAsync(o, nh * sizeof(V), w, nhp * sizeof(V), nh * sizeof(V), n1, cudaMemcpyDeviceToDevice,
-                              s) != cudaSuccess)
+        // one plane per transform: the compact output is the padded workspace without its pad column
+        if (cudaMemcpy2DAsync(o, nh * sizeof(V), w, nhp * sizeof(V), nh * sizeof(V), B * n1,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return AFFT_ERR_CUDA;
     }
     mark(p, 3, s);
@@ -627,7 +634,8 @@ int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
-    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, nhp = p->nhp;
+    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, nhp = p->nhp, B = p->batch;
+    const long long P0 = B * n0;
     const double scale = 1.0 / ((double)p->n[0] * (double)p->n[1] * (double)p->n[2]);
     // C2C works in `out`; c2r works in the plan's workspace and writes real `out` last.
     V *buf = p->kind == AFFT_C2C ? (V *)out : (V *)p->d_work;
@@ -647,22 +655,22 @@ int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
     mark(p, 0, s);
     const Remap rm = nhp != nh ? Remap{n1 * nhp, (int)nh, (int)nhp} : Remap{0, 0, 0};
     if (n0 > 1 || nhp == nh) {
-        if (axis_stage<V>(p, 0, (const V *)in, buf, 1, n1 * nh, 1, 1.0, s, rm) != cudaSuccess)
+        if (axis_stage<V>(p, 0, (const V *)in, buf, B, n1 * nh, 1, 1.0, s, rm) != cudaSuccess)
             return AFFT_ERR_CUDA;
     } else {
-        if (cudaMemcpy2DAsync(buf, nhp * sizeof(V), in, nh * sizeof(V), nh * sizeof(V), n1, cudaMemcpyDeviceToDevice,
-                              s) != cudaSuccess)
+        if (cudaMemcpy2DAsync(buf, nhp * sizeof(V), in, nh * sizeof(V), nh * sizeof(V), B * n1,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return AFFT_ERR_CUDA;
     }
     mark(p, 1, s);
     const int K = p->chunk_planes;
     if (K > 0) {
-        const long long C = (n0 + K - 1) / K;
+        const long long C = (P0 + K - 1) / K;
         cudaEvent_t *ev = p->chunk_ev.data();
         cudaError_t e = cudaEventRecord(ev[0], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, ev[0], 0);
         for (long long c = 0; c < C && e == cudaSuccess; ++c) {
-            const long long p0 = c * K, np = std::min<long long>(K, n0 - p0);
+            const long long p0 = c * K, np = std::min<long long>(K, P0 - p0);
             if (c >= 2) e = cudaStreamWaitEvent(s, ev[1 + 2 * (c - 2) + 1], 0);
             if (e == cudaSuccess) e = ystage(p0, np, s);
             if (e == cudaSuccess) e = cudaEventRecord(ev[1 + 2 * c], s);
@@ -674,9 +682,9 @@ int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
         if (e != cudaSuccess) return AFFT_ERR_CUDA;
         mark(p, 2, s);
     } else {
-        if (ystage(0, n0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        if (ystage(0, P0, s) != cudaSuccess) return AFFT_ERR_CUDA;
         mark(p, 2, s);
-        if (zstage(0, n0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        if (zstage(0, P0, s) != cudaSuccess) return AFFT_ERR_CUDA;
     }
     mark(p, 3, s);
     return AFFT_OK;
@@ -688,7 +696,7 @@ int configure_chunks(afft_plan *p, size_t bytes)
 {
     p->chunk_bytes = bytes;
     p->chunk_planes = 0;
-    const long long n0 = p->n[0], n1 = p->n[1];
+    const long long n0 = p->batch * p->n[0], n1 = p->n[1];
     const size_t plane = (size_t)n1 * p->nhp * cplx_size(p->precision);
     if (bytes == 0 || n1 <= 1 || n0 < 3 || plane == 0) return AFFT_OK;
     long long K = (long long)(bytes / plane);
@@ -711,12 +719,12 @@ int configure_chunks(afft_plan *p, size_t bytes)
 
 size_t in_bytes(const afft_plan *p)
 {
-    const size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+    const size_t N = (size_t)p->batch * p->n[0] * p->n[1] * p->n[2];
     return p->kind == AFFT_C2C ? N * cplx_size(p->precision) : N * real_size(p->precision);
 }
 size_t out_bytes(const afft_plan *p)
 {
-    return (size_t)p->n[0] * p->n[1] * p->nh * cplx_size(p->precision);
+    return (size_t)p->batch * p->n[0] * p->n[1] * p->nh * cplx_size(p->precision);
 }
 
 bool overlaps(const void *a, size_t na, const void *b, size_t nb)
@@ -733,6 +741,24 @@ int check_exec(afft_plan *p, const void *in, void *out, int backward)
     const size_t no = backward ? in_bytes(p) : out_bytes(p);
     if (overlaps(in, ni, out, no)) return AFFT_ERR_INPLACE;
     return AFFT_OK;
+}
+
+// Re-shapes the contiguous stage for `target` points per CTA.
+template <typename V>
+bool reshape_contig(afft_plan *p, int target)
+{
+    if (p->four[2].on) return false;
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if (max_smem <= 0) max_smem = 48 * 1024;
+    AxisPlan &z = p->ax[2];
+    const size_t budget = z.ks->generic ? (size_t)max_smem : (size_t)std::min(max_smem, 112 * 1024);
+    Launch L;
+    if (!shape_contig(z.desc, p->batch * p->n[0] * p->n[1], sizeof(V), z.ks->max_threads, budget, L, target))
+        return false;
+    z.launch = L;
+    p->contig_target = target;
+    return true;
 }
 
 }  // namespace
@@ -762,6 +788,11 @@ const char *afft_status_string(int status)
 
 int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precision)
 {
+    return afft_plan_create_batched(out, n, 1, kind, precision);
+}
+
+int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch, int kind, int precision)
+{
     if (!out) return AFFT_ERR_NULL;
     *out = nullptr;
     if (!n) return AFFT_ERR_NULL;
@@ -771,6 +802,7 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
     for (int i = 0; i < 3; ++i)
         if (!factor_ok(n[i])) return AFFT_ERR_SIZE;
     if (kind == AFFT_R2C && n[2] % 2 != 0) return AFFT_ERR_R2C_ODD;
+    if (batch < 1) return AFFT_ERR_SIZE;
     if (precision == AFFT_F32_SPLIT) return AFFT_ERR_UNSUPPORTED;
     const int64_t zlen = kind == AFFT_R2C ? n[2] / 2 : n[2];
     // lines longer than one CTA holds are split four-step (n = n_a n_b, both <= kMaxLine);
@@ -786,6 +818,7 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
     afft_plan *p = new (std::nothrow) afft_plan();
     if (!p) return AFFT_ERR_NOMEM;
     for (int i = 0; i < 3; ++i) p->n[i] = n[i];
+    p->batch = batch;
     p->kind = kind;
     p->precision = precision;
     p->nh = kind == AFFT_R2C ? n[2] / 2 + 1 : n[2];
@@ -852,14 +885,14 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
         }
     }
     if (st == AFFT_OK && any_four) {
-        const size_t bytes = (size_t)n[0] * n[1] * p->nhp * cplx_size(precision);
+        const size_t bytes = (size_t)batch * n[0] * n[1] * p->nhp * cplx_size(precision);
         if (cudaMalloc(&p->d_four, bytes) != cudaSuccess) {
             p->d_four = nullptr;
             st = AFFT_ERR_NOMEM;
         }
     }
     if (st == AFFT_OK && kind == AFFT_R2C) {
-        p->work_bytes = (size_t)n[0] * n[1] * p->nhp * cplx_size(precision);
+        p->work_bytes = (size_t)batch * n[0] * n[1] * p->nhp * cplx_size(precision);
         if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) {
             p->d_work = nullptr;
             p->work_bytes = 0;
@@ -994,6 +1027,135 @@ int afft_plan_device_status(afft_plan *p)
     return AFFT_ERR_TIMEOUT;
 }
 
+// ----------------------------------------------------------------- tuner --
+
+namespace {
+
+// Mean milliseconds of forward + backward over `reps` runs on the tuning buffers.
+float time_round_trip(afft_plan *p, void *in, void *spec, void *back, cudaStream_t s, int reps)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1.f;
+    }
+    float ms = -1.f;
+    if (afft_execute_forward(p, in, spec, s) == AFFT_OK && afft_execute_backward(p, spec, back, s) == AFFT_OK &&
+        cudaEventRecord(a, s) == cudaSuccess) {
+        bool ok = true;
+        for (int r = 0; r < reps && ok; ++r)
+            ok = afft_execute_forward(p, in, spec, s) == AFFT_OK && afft_execute_backward(p, spec, back, s) == AFFT_OK;
+        if (ok && cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+            ms /= (float)reps;
+        else
+            ms = -1.f;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+}  // namespace
+
+int afft_plan_tune(afft_plan *p, void *stream)
+{
+    if (!p) return AFFT_ERR_NULL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ib = in_bytes(p), ob = out_bytes(p);
+    void *in = nullptr, *spec = nullptr, *back = nullptr;
+    if (cudaMalloc(&in, ib) != cudaSuccess || cudaMalloc(&spec, ob) != cudaSuccess ||
+        cudaMalloc(&back, ib) != cudaSuccess) {
+        cudaFree(in);
+        cudaFree(spec);
+        cudaFree(back);
+        cudaGetLastError();
+        return AFFT_ERR_NOMEM;
+    }
+    const int prec = p->precision == AFFT_F64 ? AFFT_F64 : AFFT_F32;
+    const size_t c = cplx_size(p->precision);
+    int st = afft_fill_uniform(in, (int64_t)(ib / c), 0x7453ull, prec, stream);
+    const int reps = 3;
+    auto measure = [&]() { return time_round_trip(p, in, spec, back, s, reps); };
+    if (st == AFFT_OK) {
+        // 1. points per CTA of the contiguous stage
+        if (!p->four[2].on) {
+            int best_t = p->contig_target;
+            float best = measure();
+            for (int t : {1024, 2048, 4096, 8192}) {
+                const bool ok = p->precision == AFFT_F64 ? reshape_contig<double2>(p, t) : reshape_contig<float2>(p, t);
+                if (!ok) continue;
+                const float ms = measure();
+                if (ms > 0 && (best < 0 || ms < best)) {
+                    best = ms;
+                    best_t = t;
+                }
+            }
+            if (p->precision == AFFT_F64) reshape_contig<double2>(p, best_t);
+            else reshape_contig<float2>(p, best_t);
+        }
+        // 2. pipelined or plain kernels for the strided stages (the padded r2c layout needs the
+        //    pipelined N0 stage for its column remap)
+        for (int a = 1; a >= 0; --a) {
+            AxisPlan &ap = p->ax[a];
+            if (!ap.pipe_avail || (a == 0 && p->nhp != p->nh)) continue;
+            ap.pipe = true;
+            const float with = measure();
+            ap.pipe = false;
+            const float without = measure();
+            ap.pipe = !(without > 0 && (with < 0 || without < with));
+        }
+        // 3. L2 slab schedule for arrays well beyond L2
+        const size_t array = (size_t)p->batch * p->n[0] * p->n[1] * p->nhp * c;
+        if (array > ((size_t)192 << 20)) {
+            size_t best_b = 0;
+            configure_chunks(p, 0);
+            float best = measure();
+            for (size_t mb : {32, 64}) {
+                if (configure_chunks(p, mb << 20) != AFFT_OK) continue;
+                const float ms = measure();
+                if (ms > 0 && (best < 0 || ms < best)) {
+                    best = ms;
+                    best_b = mb << 20;
+                }
+            }
+            configure_chunks(p, best_b);
+        }
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = AFFT_ERR_CUDA;
+    cudaFree(in);
+    cudaFree(spec);
+    cudaFree(back);
+    return st;
+}
+
+int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
+{
+    if (!p || !buf) return AFFT_ERR_NULL;
+    char radix[3][64];
+    for (int a = 0; a < 3; ++a) {
+        const StageDesc &d = p->ax[a].desc;
+        int o = 0;
+        radix[a][0] = 0;
+        for (int i = 0; i < d.npass && o < 56; ++i) o += snprintf(radix[a] + o, 64 - o, i ? "x%d" : "%d", d.radix[i]);
+    }
+    const int need = snprintf(
+        buf, len,
+        "{\"n\": [%lld, %lld, %lld], \"batch\": %lld, \"kind\": \"%s\", \"precision\": \"%s\", "
+        "\"radix\": [\"%s\", \"%s\", \"%s\"], \"specialised\": [%d, %d, %d], \"four_step\": [%d, %d, %d], "
+        "\"pipelined\": [%d, %d], \"contig_lines\": %d, \"strided_lines\": [%d, %d], \"padded_row\": %lld, "
+        "\"l2_slab_planes\": %d}",
+        (long long)p->n[0], (long long)p->n[1], (long long)p->n[2], (long long)p->batch,
+        p->kind == AFFT_C2C ? "c2c" : "r2c", p->precision == AFFT_F64 ? "f64" : "f32", radix[0], radix[1], radix[2],
+        !p->ax[0].ks->generic, !p->ax[1].ks->generic, !p->ax[2].ks->generic, p->four[0].on, p->four[1].on,
+        p->four[2].on, p->ax[0].pipe, p->ax[1].pipe, p->ax[2].launch.lines,
+        p->ax[0].pipe ? p->ax[0].ks->pipe_lines : p->ax[0].launch.lines,
+        p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, (long long)p->nhp, p->chunk_planes);
+    if (need < 0) return AFFT_ERR_CUDA;
+    return (size_t)need < len ? AFFT_OK : AFFT_ERR_SIZE;
+}
+
 size_t afft_plan_workspace_bytes(const afft_plan *p) { return p ? p->work_bytes : 0; }
 size_t afft_plan_input_bytes(const afft_plan *p) { return p ? in_bytes(p) : 0; }
 size_t afft_plan_output_bytes(const afft_plan *p) { return p ? out_bytes(p) : 0; }
@@ -1001,7 +1163,8 @@ size_t afft_plan_output_bytes(const afft_plan *p) { return p ? out_bytes(p) : 0;
 int afft_plan_launches(const afft_plan *p, int backward)
 {
     if (!p) return 0;
-    const long long slabs = p->chunk_planes > 0 ? (p->n[0] + p->chunk_planes - 1) / p->chunk_planes : 1;
+    const long long planes = p->batch * p->n[0];
+    const long long slabs = p->chunk_planes > 0 ? (planes + p->chunk_planes - 1) / p->chunk_planes : 1;
     const int f0 = p->four[0].on, f1 = p->four[1].on, f2 = p->four[2].on && p->kind == AFFT_C2C;
     const int y = p->n[1] > 1 ? 1 + f1 : 0;
     if (backward) return (int)(1 + f0 + slabs * (1 + f2 + y));

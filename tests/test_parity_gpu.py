@@ -472,3 +472,68 @@ def test_fp64_tiny_values_mixed_with_ordinary_ones():
     report("c2c f64 tiny mixed", oracle.rel_l2(gpu_c2c(x, "f64"), oracle.c2c(x)), TOL["f64"])
     r = x.real.copy()
     report("r2c f64 tiny mixed", oracle.rel_l2(gpu_r2c(r, "f64"), oracle.r2c(r)), TOL["f64"])
+
+
+@pytest.mark.parametrize("shape,batch,kind,prec", [((24, 20, 30), 3, "c2c", "f32"), ((16, 24, 40), 5, "r2c", "f32"),
+                                                   ((12, 10, 16), 4, "r2c", "f64"), ((64, 8, 8), 2, "c2c", "f64")])
+def test_batched_plan_matches_per_field_oracle(shape, batch, kind, prec):
+    if kind == "c2c":
+        xs = np.stack([synth.uniform_complex(shape, 70 + b) for b in range(batch)]).astype(CDT[prec])
+    else:
+        xs = np.stack([synth.uniform_real(shape, 70 + b) for b in range(batch)]).astype(RDT[prec])
+    with afft.Plan(shape, kind, prec, batch=batch) as p:
+        X = p.forward(torch.from_numpy(xs).cuda())
+        y = p.backward(X)
+        torch.cuda.synchronize()
+        Xh, yh = X.cpu().numpy(), y.cpu().numpy()
+    for b in range(batch):
+        ref = oracle.c2c(xs[b]) if kind == "c2c" else oracle.r2c(xs[b])
+        report("batched %s %s %s [%d]" % (shape, kind, prec, b), oracle.rel_l2(Xh[b], ref), TOL[prec])
+        report("batched %s %s %s round trip [%d]" % (shape, kind, prec, b), oracle.rel_l2(yh[b], xs[b]), TOL[prec])
+
+
+def test_multi_plan_graph_matches_separate_executes():
+    sizes = [(48, 48, 48, 3), (64, 64, 64, 2), (120, 120, 120, 1)]
+    plans = [afft.Plan(s[:3], "r2c", "f32", batch=s[3]) for s in sizes]
+    xs = [torch.from_numpy(np.stack([synth.random_mode_field(s[:3], 80 + b, n_modes=8)
+                                     for b in range(s[3])]).astype(np.float32)).cuda() for s in sizes]
+    ref = [p.forward(x) for p, x in zip(plans, xs)]
+    refb = [p.backward(r) for p, r in zip(plans, ref)]
+    outs = [torch.empty_like(r) for r in ref]
+    backs = [torch.empty_like(x) for x in xs]
+    m = afft.Multi(plans)
+    for _ in range(3):        # capture once, then replay
+        m.forward(xs, outs)
+        m.backward(outs, backs)
+    torch.cuda.synchronize()
+    for a, b in zip(outs, ref):
+        assert torch.equal(a, b)
+    for a, b in zip(backs, refb):
+        assert torch.equal(a, b)
+    outs2 = [torch.empty_like(r) for r in ref]   # new buffers: a second graph
+    m.forward(xs, outs2)
+    torch.cuda.synchronize()
+    for a, b in zip(outs2, ref):
+        assert torch.equal(a, b)
+    m.close()
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("shape,kind,prec", [((128, 128, 128), "r2c", "f32"), ((96, 96, 96), "c2c", "f64")])
+def test_autotune_keeps_results(shape, kind, prec):
+    if kind == "c2c":
+        x = synth.uniform_complex(shape, 90).astype(CDT[prec])
+        ref = oracle.c2c(x)
+    else:
+        x = synth.uniform_real(shape, 90).astype(RDT[prec])
+        ref = oracle.r2c(x)
+    with afft.Plan(shape, kind, prec) as p:
+        before = p.describe()
+        p.tune()
+        after = p.describe()
+        assert set(after) == set(before) and after["n"] == list(shape)
+        X = p.forward(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+    print("\n[tune] %s -> %s" % (before, after))
+    report("tuned %s %s %s" % (shape, kind, prec), oracle.rel_l2(X.cpu().numpy(), ref), TOL[prec])
