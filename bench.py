@@ -318,6 +318,7 @@ def run_gpu(args):
 
     if args.extra and rank == 0:
         line["also"] = extra_configs(afft, torch, peak)
+        line["batched"] = batched_workload(afft, torch)
     if rank == 0 and world == 1 and not args.no_cpu:
         dt, b, threads, desc = cpu_oracle_sample(min_seconds=args.cpu_seconds)
         line["cpu_baseline"] = {"value": 100.0 * b / dt / 1e9 / peak, "unit": UNIT, "cores": threads,
@@ -360,6 +361,99 @@ def measure_e2e(args, plan, field, x, X, y, stream, barrier, world, step_bytes, 
     return {"value": 100.0 * world * step_bytes / (e2e_ms * 1e-3) / 1e9 / peak, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
             "call": "afft_execute_forward_host + afft_execute_backward_host"}
+
+
+def mode_field_gpu(torch, n, seed, n_modes=64, noise=1e-3):
+    """The random-mode field of synth.random_mode_field (same modes, same recipe) evaluated on the
+    GPU with torch: a rank-n_modes sum of outer products of 1-D exponentials, plus noise from a
+    seeded torch generator.  Input generation only; none of the transform's arithmetic."""
+    import numpy as np
+    from paper_1506_07933_gb300 import synth
+    ks, amp, phase = synth.draw_modes((n, n, n), n_modes, seed)
+    j = torch.arange(n, device="cuda", dtype=torch.int64)
+    def exps(d):
+        k = torch.tensor(ks[:, d], device="cuda", dtype=torch.int64)
+        ph = torch.remainder(k[:, None] * j[None, :], n).to(torch.float64)
+        return torch.exp(2j * torch.pi * ph / n)
+    e0, e1, e2 = exps(0), exps(1), exps(2)
+    c = torch.tensor(amp * np.exp(1j * phase), device="cuda")
+    f = torch.einsum("m,mi,mj,mk->ijk", c, e0, e1, e2).real
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed + 1)
+    f += noise * torch.randn(f.shape, device="cuda", dtype=torch.float64, generator=g)
+    return f.to(torch.float32)
+
+
+def batched_workload(afft, torch, steps=10, warmup=3, count=200, seed=200):
+    """200 float32 r2c fields of cubic sizes drawn from {48, 64, 96, 120, 128, 160, 256}: one
+    forward + backward of every field per step.  Three ways: one execute per field (a plan per
+    size, reused), batched plans per size run as one captured CUDA graph, and the same after
+    autotuning.  Returns solves/s (field round trips per second) for each."""
+    import collections
+    from paper_1506_07933_gb300 import synth
+    sizes = synth.batched_sizes(count, seed)
+    groups = sorted(collections.Counter(sizes).items())
+    fields = {n: torch.stack([mode_field_gpu(torch, n, seed * 1000 + 7 * n + i) for i in range(c)])
+              for n, c in groups}
+    single = {n: afft.Plan((n, n, n), "r2c", "f32") for n, _ in groups}
+    spec1 = {n: torch.empty(single[n].spectral_shape, dtype=torch.complex64, device="cuda") for n, _ in groups}
+    back1 = {n: torch.empty((n, n, n), dtype=torch.float32, device="cuda") for n, _ in groups}
+    order = [(n, i) for n, c in groups for i in range(c)]
+
+    def per_field():
+        for n, i in order:
+            single[n].forward(fields[n][i], spec1[n])
+            single[n].backward(spec1[n], back1[n])
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_single = timed(per_field)
+    results = {}
+    for tuned in (False, True):
+        plans = [afft.Plan((n, n, n), "r2c", "f32", batch=c) for n, c in groups]
+        if tuned:
+            for p in plans:
+                p.tune()
+        specs = [torch.empty(p.spectral_shape, dtype=torch.complex64, device="cuda") for p in plans]
+        backs = [torch.empty(p.spatial_shape, dtype=torch.float32, device="cuda") for p in plans]
+        ins = [fields[n] for n, _ in groups]
+        m = afft.Multi(plans)
+
+        def batched():
+            m.forward(ins, specs)
+            m.backward(specs, backs)
+
+        ms = timed(batched)
+        err = max(float(torch.linalg.vector_norm(b - x) / torch.linalg.vector_norm(x)) for b, x in zip(backs, ins))
+        results["tuned" if tuned else "batched"] = (ms, err, [p.describe() for p in plans] if tuned else None)
+        m.close()
+        for p in plans:
+            p.close()
+    for p in single.values():
+        p.close()
+    step_bytes = sum(c * 2 * sum(workload_bytes((n, n, n), 4, 8)) for n, c in groups)
+    out = {"workload": "%d float32 r2c+c2r fields, sizes %s (counts %s)" % (
+               count, [n for n, _ in groups], [c for _, c in groups]),
+           "algorithmic_bytes_per_step": step_bytes,
+           "frac_of_hbm_roofline_batched_graph": step_bytes / (results["batched"][0] * 1e-3) / 1e9 / peaks()[0],
+           "solves_per_s_one_execute_per_field": count / (ms_single * 1e-3),
+           "solves_per_s_batched_graph": count / (results["batched"][0] * 1e-3),
+           "solves_per_s_batched_graph_tuned": count / (results["tuned"][0] * 1e-3),
+           "ms_per_step": {"one_execute_per_field": ms_single, "batched_graph": results["batched"][0],
+                           "batched_graph_tuned": results["tuned"][0]},
+           "round_trip_rel_l2_max": max(results["batched"][1], results["tuned"][1])}
+    out["speedup_batched_tuned_vs_per_field"] = ms_single / results["tuned"][0]
+    return out
 
 
 def extra_configs(afft, torch, peak):
