@@ -124,6 +124,19 @@ int afft_execute_forward(afft_plan *p, const void *in, void *out, void *cuda_str
 int afft_execute_backward(afft_plan *p, const void *in, void *out, void *cuda_stream);
 
 /*
+ * Spectral Poisson solve (AccFFT Section 1 lists fast spectral operators as a
+ * feature without describing them; this is the one the serving workload
+ * uses): for an AFFT_R2C plan, u = -Laplacian^{-1} f on the periodic box
+ * [0, 2 pi)^3 with grid x_j = 2 pi j / n, i.e. u_hat(k) = f_hat(k) / |k|^2 with
+ * integer wavenumbers k_i = m (m <= n_i/2) or m - n_i, and u_hat(0) = 0 (the
+ * zero-mean solution).  in = f, out = u, both real [batch][n0][n1][n2] device
+ * arrays, out-of-place; the plan's workspace holds the spectrum.  The N0
+ * stage runs forward DFT, division and inverse DFT in one kernel when the
+ * plan's N0 stage is pipelined.  AFFT_ERR_KIND for C2C plans.  Asynchronous.
+ */
+int afft_execute_poisson(afft_plan *p, const void *in, void *out, void *cuda_stream);
+
+/*
  * The same transforms with the data in host memory: copies host_in into the
  * caller's device buffer dev_in, runs the transform into dev_out, and copies
  * dev_out back to host_out, all enqueued on the stream (pinned host memory

@@ -144,6 +144,30 @@ def dft_bins(x, ks, nthreads=None) -> np.ndarray:
     return out
 
 
+def wavenumbers(n: int) -> np.ndarray:
+    """Integer wavenumbers of the periodic grid x_j = 2 pi j / n on [0, 2 pi): m for m <= n/2,
+    else m - n (the Nyquist bin's sign does not matter for |k|^2)."""
+    m = np.arange(n)
+    return np.where(2 * m > n, m - n, m)
+
+
+def poisson(f, method: str = "fft", nthreads=None) -> np.ndarray:
+    """u with -Lap u = f on [0, 2 pi)^3, zero mean: u_hat = f_hat / |k|^2, u_hat(0) = 0.
+
+    Spectral operator on the r2c spectrum (AccFFT Section 1 names fast spectral operators; the
+    operator, grid and zero-mean convention are the readings stated for the serving workload)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    n0, n1, n2 = f.shape
+    F = r2c(f, method, nthreads)
+    k0 = wavenumbers(n0)[:, None, None]
+    k1 = wavenumbers(n1)[None, :, None]
+    k2 = np.arange(n2 // 2 + 1)[None, None, :]
+    K = (k0 * k0 + k1 * k1 + k2 * k2).astype(np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        U = np.where(K > 0, F / np.where(K > 0, K, 1.0), 0.0)
+    return c2r(U, n2, method, nthreads)
+
+
 def rel_l2(y, ref) -> float:
     """||y - ref||_2 / ||ref||_2 with float64 pairwise sums, in chunks of 2**24 values
     (both arrays divided by max|ref| first, so that squares neither overflow nor underflow)."""

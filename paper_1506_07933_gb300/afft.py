@@ -41,7 +41,7 @@ EXPORTS = [
     "afft_plan_timing_begin", "afft_plan_timing_end", "afft_c2r_noalloc",
     "afft_plan_device_status", "afft_plan_set_l2_chunk", "afft_plan_l2_chunk",
     "afft_plan_create_batched", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
-    "afft_multi_execute", "afft_multi_destroy",
+    "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson",
 ]
 
 _lib = None
@@ -66,6 +66,7 @@ def load(path: str = None):
     lib.afft_plan_create.argtypes = [ctypes.POINTER(vp), i64p, c_int, c_int]
     lib.afft_plan_create_batched.argtypes = [ctypes.POINTER(vp), i64p, ctypes.c_int64, c_int, c_int]
     lib.afft_plan_tune.argtypes = [vp, vp]
+    lib.afft_execute_poisson.argtypes = [vp, vp, vp, vp]
     lib.afft_plan_describe.argtypes = [vp, ctypes.c_char_p, sz]
     lib.afft_multi_create.argtypes = [ctypes.POINTER(vp), c_int, ctypes.POINTER(vp)]
     lib.afft_multi_execute.argtypes = [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -94,7 +95,7 @@ def load(path: str = None):
               "afft_plan_launches", "afft_fill_uniform", "afft_plan_timing_begin",
               "afft_plan_timing_end", "afft_c2r_noalloc", "afft_plan_device_status",
               "afft_plan_set_l2_chunk", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
-              "afft_multi_execute", "afft_multi_destroy"):
+              "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -244,6 +245,16 @@ class Plan:
             out = torch.empty(self.spatial_shape, dtype=self.spatial_dtype, device=self.device)
         self._check_tensor(out, self.spatial_shape, self.spatial_dtype, "output")
         afft_execute_backward(self._p, X.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def poisson(self, f, out=None, stream=None):
+        """u with -Lap u = f on [0, 2 pi)^3, zero mean (r2c plans; f real, spatial shape)."""
+        self._check_tensor(f, self.spatial_shape, self.spatial_dtype, "f")
+        if out is None:
+            out = torch.empty(self.spatial_shape, dtype=self.spatial_dtype, device=self.device)
+        self._check_tensor(out, self.spatial_shape, self.spatial_dtype, "u")
+        _check(load().afft_execute_poisson(self._p, f.data_ptr(), out.data_ptr(), _stream_handle(stream)),
+               "afft_execute_poisson")
         return out
 
     def forward_host(self, host_in, host_out, dev_in, dev_out, stream=None):

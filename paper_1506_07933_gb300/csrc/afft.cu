@@ -327,6 +327,10 @@ int plan_shapes(afft_plan *p)
             if (cudaFuncSetAttribute(ks->pipe[k], cudaFuncAttributeMaxDynamicSharedMemorySize, ks->pipe_smem) !=
                 cudaSuccess)
                 return AFFT_ERR_CUDA;
+        for (int k = 0; k < 2; ++k)
+            if (ks->poisson[k] && cudaFuncSetAttribute(ks->poisson[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       ks->pipe_smem) != cudaSuccess)
+                return AFFT_ERR_CUDA;
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks->pipe[PIPE_FWD_TMA], ks->pipe_threads,
                                                           ks->pipe_smem) != cudaSuccess || per_sm < 1)
@@ -717,6 +721,60 @@ int configure_chunks(afft_plan *p, size_t bytes)
     return AFFT_OK;
 }
 
+// Spectral Poisson solve on an R2C plan: r2c N2 and N1 stages into the
+// workspace, the fused N0 operator (or N0 forward, multiply, N0 backward),
+// N1 backward, c2r N2 with x 1/N.
+template <typename V>
+int run_poisson(afft_plan *p, const void *in, void *out, cudaStream_t s)
+{
+    using T = decltype(V().x);
+    const V *tw = (const V *)p->d_tw;
+    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, nhp = p->nhp, B = p->batch;
+    const long long P0 = B * n0;
+    const double scale = 1.0 / ((double)n0 * (double)n1 * (double)n2);
+    V *w = (V *)p->d_work;
+    mark(p, 0, s);
+    if (r2c<V, T>(p->ax[2], (const T *)in, w, tw, tw + p->post_off, P0 * n1, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n1 > 1 && axis_stage<V>(p, 1, w, w, P0, nhp, 0, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    mark(p, 1, s);
+    const AxisPlan &x = p->ax[0];
+    const long long W = n1 * nhp;
+    if (n0 > 1 && x.pipe && !p->four[0].on && x.ks->poisson[0]) {
+        alignas(64) CUtensorMap map;
+        std::memset(&map, 0, sizeof map);
+        const bool tma = encode_strided_map(&map, w, B, x.desc.n, W, sizeof(V), x.ks->pipe_lines);
+        const V *twa = tw + x.tw_base;
+        long long WW = W;
+        long long tpo = (W + x.ks->pipe_lines - 1) / x.ks->pipe_lines, nt = B * tpo;
+        const void *twdf = x.desc.twdf;
+        unsigned *err = p->d_err;
+        int in1 = (int)n1, inhp = (int)nhp, inh = (int)nh;
+        const V *win = w;
+        void *args[] = {(void *)&win, (void *)&w, (void *)&map, (void *)&twa, (void *)&WW, (void *)&tpo, (void *)&nt,
+                        (void *)&err, (void *)&twdf, (void *)&in1, (void *)&inhp, (void *)&inh};
+        const unsigned grid = (unsigned)std::min<long long>(nt, x.pipe_slots);
+        if (cudaLaunchKernel(x.ks->poisson[tma ? 0 : 1], dim3(grid), dim3(x.ks->pipe_threads), args,
+                             (size_t)x.ks->pipe_smem, s) != cudaSuccess)
+            return AFFT_ERR_CUDA;
+    } else {
+        if (n0 > 1 && axis_stage<V>(p, 0, w, w, B, W, 0, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        const KernelSet *g = p->precision == AFFT_F64 ? generic_kernels_f64() : generic_kernels_f32();
+        long long planes = P0;
+        int a0 = (int)n0, a1 = (int)n1, a2 = (int)nhp, a3 = (int)nh;
+        void *args[] = {(void *)&w, (void *)&planes, (void *)&a0, (void *)&a1, (void *)&a2, (void *)&a3};
+        const long long total = P0 * n1 * nhp;
+        const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 32);
+        if (cudaLaunchKernel(g->poisson_mult, dim3(blocks), dim3(256), args, 0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        if (n0 > 1 && axis_stage<V>(p, 0, w, w, B, W, 1, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    }
+    mark(p, 2, s);
+    if (n1 > 1 && axis_stage<V>(p, 1, w, w, P0, nhp, 1, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (c2r<V, T>(p->ax[2], w, (T *)out, tw, tw + p->post_off, P0 * n1, scale, s) != cudaSuccess)
+        return AFFT_ERR_CUDA;
+    mark(p, 3, s);
+    return AFFT_OK;
+}
+
 size_t in_bytes(const afft_plan *p)
 {
     const size_t N = (size_t)p->batch * p->n[0] * p->n[1] * p->n[2];
@@ -923,6 +981,17 @@ int afft_execute_backward(afft_plan *p, const void *in, void *out, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     return p->precision == AFFT_F64 ? run_backward<double2>(p, in, out, s)
                                     : run_backward<float2>(p, in, out, s);
+}
+
+int afft_execute_poisson(afft_plan *p, const void *in, void *out, void *stream)
+{
+    if (!p || !in || !out) return AFFT_ERR_NULL;
+    if (p->kind != AFFT_R2C) return AFFT_ERR_KIND;
+    if (in == out) return AFFT_ERR_INPLACE;
+    const size_t nb = in_bytes(p);
+    if (overlaps(in, nb, out, nb)) return AFFT_ERR_INPLACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->precision == AFFT_F64 ? run_poisson<double2>(p, in, out, s) : run_poisson<float2>(p, in, out, s);
 }
 
 static int execute_host(afft_plan *p, const void *host_in, void *host_out, void *dev_in, void *dev_out,

@@ -96,6 +96,13 @@ struct KernelSet {
     // StageDesc d, const V *tw, const V *wn, long long W, long long tiles_per_outer,
     // int log2_lines, int nb, T scale); [0] forward, [1] backward
     const void *four[2];
+    // generic family only: (V *x, long long planes, int n0, int n1, int nhp, int nh)
+    const void *poisson_mult;
+    // fused Poisson N0 stage (forward DFTs, 1/|k|^2, inverse DFTs) on pipelined tiles:
+    // (const V *in, V *out, CUtensorMap map, const V *tw, long long W,
+    // long long tiles_per_outer, long long ntiles, unsigned *err, const void *twdf,
+    // int n1, int nhp, int nh); [0] TMA, [1] cp.async
+    const void *poisson[2];
     int pipe_lines;                // columns per tile of the pipelined kernel
     int pipe_threads;              // its (compile-time) CTA size
     int pipe_smem;                 // its dynamic shared memory (two tile buffers)

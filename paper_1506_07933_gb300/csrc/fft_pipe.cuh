@@ -160,6 +160,8 @@ template <class P, typename V> struct PipeShape {
     }
     static constexpr int threads = threads_for(typename P::seq{});
     static_assert(threads % lines == 0, "each thread must own fixed columns of the tile");
+    using seq = typename P::seq;
+    static constexpr int npass = P::npass;
     static constexpr int tile = P::n * lines;                       // complex elements per tile
     static constexpr int smem = 3 * tile * (int)sizeof(V) + 16;     // 3 buffers, then two mbarriers
     static constexpr int box_rows = tma_box_rows(P::n);
@@ -387,6 +389,165 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     }
 }
 
+// ------------------------------------------------------ Poisson operator ---
+// The spectral Poisson solve -Lap u = f on [0, 2 pi)^3 divides each bin of
+// the r2c spectrum by |k|^2 (integer wavenumbers k_i = m for m <= n_i/2, else
+// m - n_i) and zeroes k = 0.  Its N0 stage is fused: forward N0 DFTs, the
+// division, inverse N0 DFTs, all on the tile in shared memory, so the
+// spectrum makes one HBM round trip instead of three.
+
+template <typename T> __device__ __forceinline__ T inv_int(int K);
+template <> __device__ __forceinline__ float inv_int<float>(int K) { return 1.0f / (float)K; }
+template <> __device__ __forceinline__ double inv_int<double>(int K) { return 1.0 / (double)K; }
+template <> __device__ __forceinline__ dfl inv_int<dfl>(int K)
+{
+    // K < 2^24 is exact in float; the FMA residual gives the low part
+    const float k = (float)K, r = 1.0f / k;
+    return dfl(r, fmaf(-r, k, 1.0f) * r);
+}
+
+// Writes of the forward half's last pass into a shared tile (both pass kinds).
+template <typename V, int LG> struct SmemTileOut {
+    SmemRowsC<V, LG> single;
+    PairSmemOut<LG> pair;
+};
+
+// Forward N0 DFTs (tile A, scratch Bf), the 1/|k|^2 scaling, inverse N0 DFTs,
+// the last pass storing through `gout`.  The thread's column is fixed
+// (tid mod LINES), so its (k1, k2) are resolved once: col1 = k1, col2 = k2,
+// keep = false for pad columns.
+template <class Sh, int N, typename CT, class GOut>
+__device__ __forceinline__ void poisson_tile(CT *A, CT *Bf, const CT *tw, const GOut &gout, int n1, int k1,
+                                             int k2, bool keep)
+{
+    using T = typename RealOf<CT>::T;
+    constexpr int LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
+    constexpr int NP = Sh::npass;
+    CT *D = (NP - 1) % 2 == 0 ? Bf : A;       // where the forward half's last pass writes
+    CT *E = D == Bf ? A : Bf;
+    SmemTileOut<CT, LG> mid;
+    mid.single = SmemRowsC<CT, LG>{D};
+    mid.pair = PairSmemOut<LG>{reinterpret_cast<float2 *>(D)};
+    pipe_passes<Sh, -1, N, 1, 0, 0>(typename Sh::seq{}, A, Bf, tw, mid);
+    __syncthreads();
+    const int k1w = 2 * k1 > n1 ? k1 - n1 : k1;
+    for (int e = threadIdx.x; e < TILE; e += NT) {
+        const int p = e >> LG;                 // k0 (natural order after the forward passes)
+        const int k0w = 2 * p > N ? p - N : p;
+        const int K = k0w * k0w + k1w * k1w + k2 * k2;
+        D[e] = (keep && K > 0) ? cscale(D[e], inv_int<T>(K)) : czero<CT>();
+    }
+    __syncthreads();
+    pipe_passes<Sh, +1, N, 1, 0, 0>(typename Sh::seq{}, D, E, tw, gout);
+}
+
+template <class P, typename V, bool TMA>
+__global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
+    k_poisson_pipe(const V *__restrict__ in, V *out, const __grid_constant__ CUtensorMap tmap,
+                   const V *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
+                   unsigned *err, const void *twdf, int n1, int nhp, int nh)
+{
+    using Sh = PipeShape<P, V>;
+    constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
+    constexpr unsigned TILE_BYTES = TILE * sizeof(V);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    V *const buf0 = reinterpret_cast<V *>(smem_raw);
+    V *const scratch = buf0 + 2 * TILE;
+    unsigned long long *const bars = reinterpret_cast<unsigned long long *>(smem_raw + 3 * TILE_BYTES);
+    const int tid = threadIdx.x;
+
+    long long t = blockIdx.x;
+    if (t >= ntiles) return;
+    if (TMA && tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](long long tile, int b) {
+        const long long o = tile / tiles_per_outer;
+        const long long c0 = (tile - o * tiles_per_outer) * LINES;
+        if constexpr (TMA) {
+            if (tid == 0) {
+                fence_async_shared();
+                mbar_expect_tx(&bars[b], TILE_BYTES);
+                constexpr int rows = Sh::box_rows;
+                constexpr int per = (int)sizeof(V) / 8;
+#pragma unroll
+                for (int r0 = 0; r0 < N; r0 += rows)
+                    tma_load_3d(buf0 + b * TILE + r0 * LINES, &tmap, (int)(c0 * per), r0, (int)o, &bars[b]);
+            }
+        } else {
+            const V *src = in + o * (long long)N * W + c0;
+            const int valid = (int)min((long long)LINES, W - c0);
+            for (int e = tid; e < TILE; e += NT) {
+                const int p = e >> LG, l = e & (LINES - 1);
+                const bool ok = l < valid;
+                cp_async_zfill<(int)sizeof(V)>(buf0 + b * TILE + e,
+                                               ok ? (const void *)(src + (long long)p * W + l) : (const void *)src,
+                                               ok);
+            }
+            cp_async_commit();
+        }
+    };
+
+    issue(t, 0);
+    for (int i = 0;; ++i) {
+        const int b = i & 1;
+        if constexpr (TMA) {
+            const bool ok = mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1));
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicExch(err, 1u);
+                return;
+            }
+        } else {
+            cp_async_wait<0>();
+            __syncthreads();
+        }
+        const long long tn = t + gridDim.x;
+        if (tn < ntiles) issue(tn, b ^ 1);
+
+        const long long o = t / tiles_per_outer;
+        const long long c0 = (t - o * tiles_per_outer) * LINES;
+        const long long c = c0 + (tid & (LINES - 1));
+        const int k1 = (int)(c / nhp), k2 = (int)(c - (long long)(c / nhp) * nhp);
+        const bool keep = c < W && k2 < nh;
+        V *X = buf0 + b * TILE;
+        V *obase = out + o * (long long)N * W;
+        bool done = false;
+        if constexpr (std::is_same<V, double2>::value) {
+            if (twdf) {
+                // float-float: convert the tile into the scratch buffer, vote on range
+                DfFlags f;
+                dcx *Y = reinterpret_cast<dcx *>(scratch);
+                for (int e = tid; e < TILE; e += NT) Y[e] = Conv<dcx, double2>::in(X[e], &f);
+                if (df_tile_ok(f)) {
+                    TileOut<V, dcx> g;
+                    g.single = GlobalColRemapOut<V, dcx>{obase, W, c < W ? c : -1};
+                    poisson_tile<Sh, N>(Y, reinterpret_cast<dcx *>(X), (const dcx *)twdf, g, n1, k1, k2, keep);
+                    done = true;
+                }
+            }
+        }
+        if (!done) {
+            TileOut<V> g;
+            g.single = GlobalColRemapOut<V>{obase, W, c < W ? c : -1};
+            if constexpr (sizeof(V) == 8) {
+                const int lp = tid % (LINES / 2 > 0 ? LINES / 2 : 1);
+                const long long a = c0 + 2 * lp;
+                float2 *base = reinterpret_cast<float2 *>(obase);
+                const bool vec = a + 1 < W && (a % 2) == 0 && (W % 2) == 0 &&
+                                 (reinterpret_cast<unsigned long long>(base) & 15) == 0;
+                g.pair = PairGlobalOut{base, W, a < W ? a : -1, a + 1 < W ? a + 1 : -1, vec};
+            }
+            poisson_tile<Sh, N>(X, scratch, tw, g, n1, k1, k2, keep);
+        }
+        __syncthreads();   // the next tile's load into this buffer waits for every read
+        if (tn >= ntiles) break;
+        t = tn;
+    }
+}
+
 // The kernels of one family as untyped entry points for the host.
 template <class F, typename V> KernelSet kernel_set(int n, int npass, const int *radix)
 {
@@ -405,6 +566,7 @@ template <class F, typename V> KernelSet kernel_set(int n, int npass, const int 
     if constexpr (F::generic) {
         k.four[0] = (const void *)k_fourstep<-1, V>;
         k.four[1] = (const void *)k_fourstep<+1, V>;
+        k.poisson_mult = (const void *)k_poisson_mult<V>;
     }
     if constexpr (!F::generic) {
         // n = 1024 would need 64-byte tile rows to double-buffer; measured slower than the
@@ -416,6 +578,8 @@ template <class F, typename V> KernelSet kernel_set(int n, int npass, const int 
             k.pipe[PIPE_FWD_CPASYNC] = (const void *)k_strided_pipe<P, -1, V, false>;
             k.pipe[PIPE_BWD_TMA] = (const void *)k_strided_pipe<P, +1, V, true>;
             k.pipe[PIPE_BWD_CPASYNC] = (const void *)k_strided_pipe<P, +1, V, false>;
+            k.poisson[0] = (const void *)k_poisson_pipe<P, V, true>;
+            k.poisson[1] = (const void *)k_poisson_pipe<P, V, false>;
             k.pipe_lines = Sh::lines;
             k.pipe_threads = Sh::threads;
             k.pipe_smem = Sh::smem;

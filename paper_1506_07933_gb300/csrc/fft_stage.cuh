@@ -450,6 +450,27 @@ __global__ void __launch_bounds__(256, 1)
     run_generic<S, true, false>(d, tw, sm, lines, log2_lines, MapLineFast{log2_lines}, src, dst);
 }
 
+// Spectral Poisson multiply on a half spectrum [planes][n1][nhp] (planes =
+// batch * n0): bin (k0, k1, k2) times 1/|k|^2 with wrapped integer wavenumbers,
+// k = 0 and pad columns (k2 >= nh) set to zero.  Used when the N0 stage of a
+// plan cannot run the fused pipelined operator.
+template <typename V>
+__global__ void k_poisson_mult(V *x, long long planes, int n0, int n1, int nhp, int nh)
+{
+    using T = typename RealOf<V>::T;
+    const long long total = planes * n1 * nhp;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k2 = (int)(i % nhp);
+        const long long r = i / nhp;
+        const int k1 = (int)(r % n1);
+        const int k0 = (int)((r / n1) % n0);
+        const int a = 2 * k0 > n0 ? k0 - n0 : k0, b = 2 * k1 > n1 ? k1 - n1 : k1;
+        const int K = a * a + b * b + k2 * k2;
+        x[i] = (K > 0 && k2 < nh) ? cscale(x[i], T(1) / T(K)) : czero<V>();
+    }
+}
+
 // Line lengths with specialised kernels and their radix sequences (n first,
 // then the radices in pass order).
 #define AFFT_LINE_PLANS(X)                                                                          \

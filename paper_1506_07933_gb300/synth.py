@@ -92,6 +92,17 @@ def random_mode_field(shape, seed: int, n_modes: int = 64, noise: float = 1e-3,
     return f
 
 
+def manufactured_poisson(shape, seed: int, n_modes: int = 16):
+    """A zero-mean u = sum of n_modes random modes a cos(k.x + phi) with |k| <= min(n)/4 and the
+    matching f = -Lap u = sum |k|^2 a cos(k.x + phi), both in float64.  Returns (f, u)."""
+    shape = tuple(int(s) for s in shape)
+    ks, amp, phase = draw_modes(shape, n_modes, seed)
+    u = mode_sum(shape, ks, amp, phase)
+    k2 = (ks * ks).sum(axis=1).astype(np.float64)
+    f = mode_sum(shape, ks, amp * k2, phase)
+    return f, u
+
+
 def splitmix64(x: np.ndarray) -> np.ndarray:
     """splitmix64 output for state values x (uint64 array), wrapping arithmetic."""
     with np.errstate(over="ignore"):
