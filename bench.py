@@ -319,6 +319,7 @@ def run_gpu(args):
     if args.extra and rank == 0:
         line["also"] = extra_configs(afft, torch, peak)
         line["batched"] = batched_workload(afft, torch)
+        line["serving"] = serving_workload(torch)
     if rank == 0 and world == 1 and not args.no_cpu:
         dt, b, threads, desc = cpu_oracle_sample(min_seconds=args.cpu_seconds)
         line["cpu_baseline"] = {"value": 100.0 * b / dt / 1e9 / peak, "unit": UNIT, "cores": threads,
@@ -453,6 +454,35 @@ def batched_workload(afft, torch, steps=10, warmup=3, count=200, seed=200):
                            "batched_graph_tuned": results["tuned"][0]},
            "round_trip_rel_l2_max": max(results["batched"][1], results["tuned"][1])}
     out["speedup_batched_tuned_vs_per_field"] = ms_single / results["tuned"][0]
+    return out
+
+
+def serving_workload(torch, count=400, rate=200.0, saturation=200, loaded=700.0):
+    """Spectral Poisson requests (sizes uniform over 64..512 cubed, 30% FP64, Poisson arrivals at
+    `rate` per second): the continuous-batching server against one request at a time, in real time,
+    then both again at `loaded` requests per second (near the GPU's capacity) and with every request
+    arriving at once (saturation).  Every solution is checked
+    against its closed form after the timed run."""
+    from paper_1506_07933_gb300 import serve
+    sizes = serve.SIZES
+    pool = serve.RhsPool(sizes)
+    out = {"workload": "Poisson solves -Lap u = f on [0,2pi)^3, n uniform over %s, 30%% float64, "
+                       "f from 16 random modes, resident in HBM before the clock starts" % (sizes,)}
+    for tag, n_req, r in (("at_%g_per_s" % rate, count, rate), ("at_%g_per_s" % loaded, count, loaded),
+                          ("saturation", saturation, 0.0)):
+        srv = serve.PoissonServer(pool, slots=4)
+        srv.warm(sizes)
+        reqs = serve.poisson_requests(n_req, rate=r, sizes=sizes, seed=5)
+        got, wall = srv.run(reqs)
+        srv.close()
+        torch.cuda.empty_cache()
+        served = serve.summarize(got, wall)
+        reqs = serve.poisson_requests(n_req, rate=r, sizes=sizes, seed=5)
+        got, wall = serve.run_plain(pool, reqs, warm_sizes=sizes)
+        torch.cuda.empty_cache()
+        plain = serve.summarize(got, wall)
+        out[tag] = {"batched_server": {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in served.items()},
+                    "one_at_a_time": {k: (float("%.4g" % v) if isinstance(v, float) else v) for k, v in plain.items()}}
     return out
 
 

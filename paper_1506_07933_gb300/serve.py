@@ -1,0 +1,379 @@
+"""A request loop for spectral Poisson solves on one GPU (continuous batching).
+
+Requests (grid size n, precision, a right-hand side f already resident in
+device memory) arrive over time.  The server keeps plans, twiddles,
+workspaces and output buffers resident on the device and, at every
+scheduling step:
+
+* polls completion events, records latency (arrival -> solution ready) and
+  frees the stream slot;
+* takes the oldest waiting (n, precision) queue first and, while a stream
+  slot is free and the HBM budget (bytes of plans plus buffers the server
+  holds) allows, groups up to a per-size cap of its requests (a power of two)
+  into one batched solve: one batched plan, one `afft_execute_poisson` on the
+  slot's stream.  A batch gathers its members' right-hand sides into the
+  plan's contiguous input (a device copy); a single request is solved in
+  place from its own buffer;
+* groups of different sizes run on different streams and overlap on the GPU.
+
+`run_plain` serves the same requests one at a time on one stream with a
+(cached) single plan per size: the plain one-plan-per-request form the
+batched server is compared with.
+
+Right-hand sides come from `RhsPool`: per (n, precision) a few manufactured
+fields f = -Lap u with u a sum of random Fourier modes, generated on the
+device before the run (outside the measured latency).  Each solution is
+checked against its closed-form u after the run.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import afft, synth
+
+DT = {"f32": torch.float32, "f64": torch.float64}
+BYTES = {"f32": 4, "f64": 8}
+SIZES = (64, 128, 192, 256, 384, 512)
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the run
+    n: int
+    precision: str
+    sample: int             # which right-hand side of the pool (per n)
+    # filled in by the server
+    start: float = math.nan
+    done: float = math.nan
+    error: float = math.nan
+    batch: int = 0
+
+
+def poisson_requests(count: int, rate: float = 200.0, sizes=SIZES, f64_share=0.3, samples: int = 4,
+                     seed: int = 5):
+    """Poisson arrivals (exponential inter-arrival times at `rate` per second; all at t = 0 when
+    rate is 0), sizes uniform over `sizes`, precision f64 with probability `f64_share`, right-hand
+    side uniform over `samples` pool entries."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        n = int(sizes[rng.integers(0, len(sizes))])
+        prec = "f64" if rng.random() < f64_share else "f32"
+        out.append(Request(i, t, n, prec, int(rng.integers(0, samples))))
+    return out
+
+
+def _mode_sum_gpu(n, ks, amp, phase, dtype, out=None):
+    """sum_m amp_m cos(k_m . x + phase_m) on the n^3 grid x_j = 2 pi j / n, evaluated on the device in
+    `dtype` as one real matrix product: with A[ij, m] = c_m e0[m, i] e1[m, j] (c_m = amp_m exp(i phase_m))
+    and E2[m, k] = e2[m, k], Re(A E2) = [Re A, -Im A] [Re E2; Im E2].  Input generation only: none of
+    the transform's arithmetic."""
+    # one non-blocking copy of the modes (wavevectors are small integers, exact in float64)
+    host = np.concatenate([ks.astype(np.float64), amp[:, None], phase[:, None]], axis=1)
+    dev = torch.from_numpy(host).pin_memory().to("cuda", non_blocking=True)
+    k, a, ph = dev[:, :3].long(), dev[:, 3], dev[:, 4]
+    j = torch.arange(n, device="cuda", dtype=torch.int64)
+    e = [torch.exp(2j * math.pi * torch.remainder(k[:, d, None] * j[None, :], n).double() / n) for d in range(3)]
+    c = torch.polar(a, ph)
+    A = (c[:, None, None] * e[0][:, :, None] * e[1][:, None, :]).reshape(len(c), n * n)
+    left = torch.cat([A.real, -A.imag], 0).t().to(dtype)           # [n^2, 2M]
+    right = torch.cat([e[2].real, e[2].imag], 0).to(dtype)          # [2M, n]
+    if out is None:
+        out = torch.empty((n, n, n), dtype=dtype, device="cuda")
+    torch.matmul(left, right, out=out.view(n * n, n))
+    return out
+
+
+class RhsPool:
+    """Per n, `samples` manufactured right-hand sides f = -Lap u = sum |k|^2 a cos(k.x + phi)
+    (16 modes, |k| <= n/4, drawn by `synth.draw_modes` with seed base + 7919 n + s), held on the
+    device in every requested precision (the float64 field rounded once)."""
+
+    def __init__(self, sizes=SIZES, precisions=("f32", "f64"), samples: int = 4, base: int = 1000,
+                 n_modes: int = 16):
+        self.samples, self.base, self.n_modes = samples, base, n_modes
+        self.f = {}
+        for n in sizes:
+            for s in range(samples):
+                ks, amp, phase = self.modes(n, s)
+                k2 = (ks * ks).sum(axis=1).astype(np.float64)
+                f64 = _mode_sum_gpu(n, ks, amp * k2, phase, torch.float64)
+                for prec in precisions:
+                    self.f[(n, prec, s)] = f64 if prec == "f64" else f64.to(DT[prec])
+        torch.cuda.synchronize()
+
+    def modes(self, n, s):
+        return synth.draw_modes((n,) * 3, self.n_modes, self.base + 7919 * n + s)
+
+    def rhs(self, req):
+        return self.f[(req.n, req.precision, req.sample)]
+
+    def solution(self, n, s):
+        """The closed-form u of sample s at size n, float64, on the device."""
+        ks, amp, phase = self.modes(n, s)
+        return _mode_sum_gpu(n, ks, amp, phase, torch.float64)
+
+
+def check(pool, reqs, result):
+    """Relative L2 error of each request's solution (`result(req)` -> device tensor) against its
+    closed form; one closed form per distinct (n, sample)."""
+    by = collections.defaultdict(list)
+    for r in reqs:
+        by[(r.n, r.sample)].append(r)
+    for (n, s), rs in by.items():
+        ref = pool.solution(n, s)
+        norm = torch.linalg.vector_norm(ref)
+        for r in rs:
+            r.error = float(torch.linalg.vector_norm(result(r).double() - ref) / norm)
+        del ref
+
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return math.nan
+    k = min(len(xs) - 1, max(0, int(math.ceil(q / 100.0 * len(xs))) - 1))
+    return xs[k]
+
+
+def summarize(reqs, wall):
+    lat = [(r.done - r.arrival) * 1e3 for r in reqs]
+    return {"requests": len(reqs), "wall_s": wall, "solves_per_s": len(reqs) / wall if wall > 0 else math.nan,
+            "p50_ms": _percentile(lat, 50), "p99_ms": _percentile(lat, 99), "max_ms": max(lat) if lat else math.nan,
+            "max_rel_error": max(r.error for r in reqs) if reqs else math.nan,
+            "mean_batch": float(np.mean([r.batch for r in reqs])) if reqs else math.nan}
+
+
+class PoissonServer:
+    """Continuous-batching Poisson server (see the module docstring)."""
+
+    def __init__(self, pool: RhsPool, slots: int = 4, hbm_budget: int = None, max_batch_bytes: int = 64 << 20,
+                 max_batch: int = 16):
+        self.pool = pool
+        self.slots = [torch.cuda.Stream() for _ in range(slots)]
+        free, _ = torch.cuda.mem_get_info()
+        self.budget = hbm_budget if hbm_budget is not None else int(free * 0.6)
+        self.max_batch_bytes = max_batch_bytes
+        self.max_batch = max_batch
+        self.plans = {}           # (n, prec, B) -> [idle (plan, f, u)]
+        self.held = 0             # bytes of plans and buffers the server holds
+        self.results = {}
+
+    def _cap(self, n, prec):
+        one = n ** 3 * BYTES[prec]
+        return max(1, min(self.max_batch, self.max_batch_bytes // one))
+
+    def _batch(self, n, prec, waiting):
+        """Largest power of two <= min(waiting, cap): few distinct batched plans per size."""
+        B = 1
+        while 2 * B <= min(waiting, self._cap(n, prec)):
+            B *= 2
+        return B
+
+    def _footprint(self, n, prec, B):
+        # u, plan workspace (half spectrum, padded), and f for a batch (a single request is solved
+        # from its own buffer); twiddles are small
+        return B * n ** 3 * BYTES[prec] * (2 if B > 1 else 1) + B * n * n * (n // 2 + 2) * 2 * BYTES[prec]
+
+    def _evict(self, need, keep):
+        """Free idle plans and buffers of other keys (largest first) until `need` more bytes fit."""
+        idle = sorted((k for k, ps in self.plans.items() if ps and k != keep), key=lambda k: -self._footprint(*k))
+        for k in idle:
+            while self.plans[k] and self.held + need > self.budget:
+                self.plans[k].pop()[0].close()
+                self.held -= self._footprint(*k)
+            if self.held + need <= self.budget:
+                break
+        if self.held + need <= self.budget:
+            torch.cuda.empty_cache()
+            return True
+        return False
+
+    def _take(self, n, prec, B):
+        key = (n, prec, B)
+        idle = self.plans.setdefault(key, [])
+        if not idle:
+            need = self._footprint(n, prec, B)
+            if need > self.budget:
+                raise MemoryError("a %d^3 %s batch of %d does not fit the HBM budget" % (n, prec, B))
+            if self.held + need > self.budget and not self._evict(need, key):
+                return None
+            p = afft.Plan((n, n, n), "r2c", prec, batch=B if B > 1 else None)
+            shape = (B, n, n, n) if B > 1 else (n, n, n)
+            f = torch.empty(shape, dtype=DT[prec], device="cuda") if B > 1 else None
+            u = torch.empty(shape, dtype=DT[prec], device="cuda")
+            self.held += need
+            idle.append((p, f, u))
+        return idle.pop()
+
+    def _give(self, key, entry):
+        self.plans[key].append(entry)
+
+    def _launch(self, group, entry, stream):
+        plan, f, u = entry
+        with torch.cuda.stream(stream):
+            if len(group) == 1:
+                src = self.pool.rhs(group[0])
+            else:
+                for b, r in enumerate(group):
+                    f[b].copy_(self.pool.rhs(r), non_blocking=True)
+                src = f
+            plan.poisson(src, u, stream=stream)
+
+    def warm(self, sizes, precisions=("f32", "f64")):
+        """Create (and run once on every slot stream) the plans the batch sizes of these sizes need,
+        so that no plan is created and no kernel first loaded inside a timed run."""
+        for n in sizes:
+            for prec in precisions:
+                B = 1
+                while B <= self._cap(n, prec):
+                    entry = self._take(n, prec, B)
+                    if entry is None:
+                        return
+                    group = [Request(-1, 0.0, n, prec, b % self.pool.samples) for b in range(B)]
+                    for s in self.slots:
+                        self._launch(group, entry, s)
+                        s.synchronize()
+                    self._give((n, prec, B), entry)
+                    B *= 2
+        torch.cuda.synchronize()
+
+    def close(self):
+        torch.cuda.synchronize()
+        for entries in self.plans.values():
+            for p, _, _ in entries:
+                p.close()
+        self.plans.clear()
+        self.held = 0
+
+    def run(self, requests, check_results=True, keep_results=False):
+        """Serve `requests` in real time; returns (requests with times filled in, wall seconds).
+        keep_results: copy each solution out at completion into `self.results[rid]` (output
+        buffers are reused by later requests)."""
+        self.results = {}
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        queue = collections.defaultdict(collections.deque)   # (n, prec) -> waiting requests
+        busy = {}                                            # slot index -> (event, group, entry, key)
+        done = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while pending or any(queue.values()) or busy:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                r = pending.popleft()
+                queue[(r.n, r.precision)].append(r)
+            for si in list(busy):
+                ev, group, entry, key = busy[si]
+                if ev.query():
+                    t = time.perf_counter() - t0
+                    u = entry[2]
+                    for b, r in enumerate(group):
+                        r.done = t
+                        if keep_results:
+                            self.results[r.rid] = (u[b] if len(group) > 1 else u).clone()
+                    self._give(key, entry)
+                    done.append((group, key))
+                    del busy[si]
+            free_slots = [i for i in range(len(self.slots)) if i not in busy]
+            for _, (n, prec) in sorted((q[0].arrival, k) for k, q in queue.items() if q):
+                if not free_slots:
+                    break
+                q = queue[(n, prec)]
+                B = self._batch(n, prec, len(q))
+                entry = self._take(n, prec, B)
+                if entry is None:
+                    continue
+                group = [q.popleft() for _ in range(B)]
+                si = free_slots.pop(0)
+                t = time.perf_counter() - t0
+                for r in group:
+                    r.start, r.batch = t, B
+                self._launch(group, entry, self.slots[si])
+                ev = torch.cuda.Event()
+                ev.record(self.slots[si])
+                busy[si] = (ev, group, entry, (n, prec, B))
+            if not busy and not any(queue.values()) and pending:
+                time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.0005)))
+        wall = time.perf_counter() - t0
+        served = [r for g, _ in done for r in g]
+        if check_results:
+            self._check_all(done)
+        return served, wall
+
+    def _check_all(self, done):
+        # output buffers are reused, so each group is re-run alone and its members kept for the check
+        torch.cuda.synchronize()
+        out = {}
+
+        def flush():
+            check(self.pool, [r for g, _ in done for r in g if r.rid in out], lambda r: out[r.rid])
+            out.clear()
+
+        for group, key in done:
+            entry = self._take(*key)
+            self._launch(group, entry, torch.cuda.current_stream())
+            u = entry[2]
+            for b, r in enumerate(group):
+                out[r.rid] = (u[b] if len(group) > 1 else u).clone()
+            self._give(key, entry)
+            if sum(t.numel() * t.element_size() for t in out.values()) > (8 << 30):
+                flush()
+        flush()
+
+
+def run_plain(pool: RhsPool, requests, check_results=True, warm_sizes=None):
+    """One request at a time on the current stream with a cached single plan per (n, precision),
+    solved in place from the request's own right-hand side.  `warm_sizes` creates those plans (and
+    runs them once) before the clock starts."""
+    plans = {}
+    reqs = sorted(requests, key=lambda r: r.arrival)
+
+    def setup(r):
+        key = (r.n, r.precision)
+        if key not in plans:
+            plans[key] = (afft.Plan((r.n,) * 3, "r2c", r.precision),
+                          torch.empty((r.n,) * 3, dtype=DT[r.precision], device="cuda"))
+        return plans[key]
+
+    for n in warm_sizes or ():
+        for prec in ("f32", "f64"):
+            w = Request(-1, 0.0, n, prec, 0)
+            plan, u = setup(w)
+            plan.poisson(pool.rhs(w), u)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        while time.perf_counter() - t0 < r.arrival:
+            pass
+        plan, u = setup(r)
+        r.start = time.perf_counter() - t0
+        r.batch = 1
+        plan.poisson(pool.rhs(r), u)
+        torch.cuda.synchronize()
+        r.done = time.perf_counter() - t0
+    wall = time.perf_counter() - t0
+    if check_results:
+        results = {}
+
+        def flush():
+            check(pool, [x for x in reqs if x.rid in results], lambda x: results[x.rid])
+            results.clear()
+
+        for r in reqs:
+            plan, _ = setup(r)
+            results[r.rid] = plan.poisson(pool.rhs(r))
+            if sum(t.numel() * t.element_size() for t in results.values()) > (8 << 30):
+                flush()
+        flush()
+    for p, _ in plans.values():
+        p.close()
+    return reqs, wall
