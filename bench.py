@@ -489,7 +489,7 @@ def serving_workload(torch, count=400, rate=200.0, saturation=200, loaded=700.0)
 def extra_configs(afft, torch, peak):
     """The other roofline configurations of the metric, fewer repetitions, same method."""
     out = []
-    for shape, kind, prec in (((512,) * 3, "r2c", "f64"), ((512,) * 3, "c2c", "f32"),
+    for shape, kind, prec in (((512,) * 3, "r2c", "f32"), ((512,) * 3, "r2c", "f64"), ((512,) * 3, "c2c", "f32"),
                               ((512,) * 3, "c2c", "f64"), ((1024,) * 3, "c2c", "f32")):
         p = afft.Plan(shape, kind, prec)
         x = torch.empty(p.spatial_shape, dtype=p.spatial_dtype, device="cuda")
@@ -521,6 +521,18 @@ def extra_configs(afft, torch, peak):
         ms = e0.elapsed_time(e1) / reps
         out.append({"workload": "%s %dx%dx%d %s fwd+bwd" % ((kind,) + shape + (prec,)), "ms_per_step": ms,
                     "frac_of_hbm_roofline": 2 * b / (ms * 1e-3) / 1e9 / peak})
+        if kind == "r2c":
+            # the fused spectral Poisson solve on the same field: 5 array passes (r2c N2, N1; fused
+            # N0 forward / 1/|k|^2 / inverse; c2r N1, N2) against the 6 of forward + backward
+            e0.record()
+            for _ in range(reps):
+                p.poisson(x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            pms = e0.elapsed_time(e1) / reps
+            out.append({"workload": "poisson %dx%dx%d %s (fused N0 stage)" % (shape + (prec,)), "ms_per_step": pms,
+                        "frac_of_hbm_roofline_6pass": 2 * b / (pms * 1e-3) / 1e9 / peak,
+                        "ms_fwd_plus_bwd": ms})
         del x, X, y
         p.close()
         torch.cuda.empty_cache()
