@@ -490,7 +490,8 @@ def extra_configs(afft, torch, peak):
     """The other roofline configurations of the metric, fewer repetitions, same method."""
     out = []
     for shape, kind, prec in (((512,) * 3, "r2c", "f32"), ((512,) * 3, "r2c", "f64"), ((512,) * 3, "c2c", "f32"),
-                              ((512,) * 3, "c2c", "f64"), ((1024,) * 3, "c2c", "f32")):
+                              ((512,) * 3, "c2c", "f64"), ((1024,) * 3, "c2c", "f32"),
+                              ((1024,) * 3, "c2c", "f32_split")):
         p = afft.Plan(shape, kind, prec)
         x = torch.empty(p.spatial_shape, dtype=p.spatial_dtype, device="cuda")
         if kind == "c2c":

@@ -62,8 +62,13 @@ typedef struct afft_plan afft_plan;
 enum { AFFT_C2C = 0, AFFT_R2C = 1 };
 
 /* Precisions (AccFFT Section 1: single and double precision).
- * AFFT_F32_SPLIT is reserved for a split-precision tensor-core path and is
- * rejected with AFFT_ERR_UNSUPPORTED by this version. */
+ * AFFT_F32_SPLIT: complex64/float32 data like AFFT_F32, with every radix-16
+ * pass computed on the tensor cores as FP16 matrix products of hi + lo split
+ * operands (a hi*hi + hi*lo + lo*hi, FP32 accumulation, each butterfly scaled
+ * by a power of two into FP16 range); other radices run in FP32.  Relative L2
+ * error <= 2e-5 against the exact transform.  The paper supports single and
+ * double precision only and names mixed floating-point computation as missing
+ * (the limitations at the end of Section 2); this mode is that extension. */
 enum { AFFT_F32 = 0, AFFT_F64 = 1, AFFT_F32_SPLIT = 2 };
 
 enum {
@@ -91,7 +96,7 @@ enum {
  *   out:       receives the plan (set to NULL on failure).
  *   n:         host array of 3 sizes, slowest first.
  *   kind:      AFFT_C2C or AFFT_R2C.
- *   precision: AFFT_F32 or AFFT_F64.
+ *   precision: AFFT_F32, AFFT_F64 or AFFT_F32_SPLIT.
  * Synchronises the current device once (twiddle upload) before returning.
  */
 int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precision);

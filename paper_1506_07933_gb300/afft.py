@@ -168,8 +168,8 @@ def afft_c2r_noalloc(shape, precision: int, in_ptr: int, out_ptr: int, stream: i
 
 # --------------------------------------------------------------- tensor API --
 
-_CDT = {F32: torch.complex64, F64: torch.complex128}
-_RDT = {F32: torch.float32, F64: torch.float64}
+_CDT = {F32: torch.complex64, F64: torch.complex128, F32_SPLIT: torch.complex64}
+_RDT = {F32: torch.float32, F64: torch.float64, F32_SPLIT: torch.float32}
 
 
 class Plan:

@@ -66,6 +66,7 @@ struct afft_plan {
     // the N1 stage of slab c on a second stream while the N2 stage of slab c+1 runs
     FourStep four[3];      // per axis
     void *d_four;          // four-step intermediate: n0*n1*nhp complex
+    unsigned *d_mma;       // split-precision plans: DFT-16 tensor-core fragments
     int contig_target;     // points per CTA of the contiguous stage (0: default)
     size_t chunk_bytes;    // requested slab size (0: off)
     int chunk_planes;      // planes per slab; 0 when the stages run unfused
@@ -123,6 +124,13 @@ bool four_step_split(int64_t n, int &na, int &nb)
 
 const KernelSet *lookup_kernels(int precision, int64_t n)
 {
+    if (precision == AFFT_F32_SPLIT) {
+        // split-precision sequences where the length has radix-16 passes; the FP32 kernels
+        // (which then compute the same) for the other specialised lengths
+        if (const KernelSet *k = spec_kernels_split((int)n)) return k;
+        if (const KernelSet *k = spec_kernels_f32((int)n)) return k;
+        return generic_kernels_split();
+    }
     const KernelSet *k = precision == AFFT_F64 ? spec_kernels_f64((int)n) : spec_kernels_f32((int)n);
     if (k) return k;
     return precision == AFFT_F64 ? generic_kernels_f64() : generic_kernels_f32();
@@ -456,9 +464,10 @@ cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, lo
     long long wout = rm.in > 0 ? rm.Wout : W;
     int rin = rm.in, rout = rm.out;
     const void *twdf = a.desc.twdf;
+    const unsigned *mma = a.desc.mma;
     const unsigned grid = (unsigned)std::min<long long>(nt, a.pipe_slots);
-    void *args[] = {(void *)&in, (void *)&out, (void *)&map, (void *)&tw, (void *)&W, (void *)&tpo, (void *)&nt,
-                    (void *)&err, (void *)&wout, (void *)&rin, (void *)&rout, (void *)&twdf};
+    void *args[] = {(void *)&in,   (void *)&out,  (void *)&map,  (void *)&tw,   (void *)&W,    (void *)&tpo, (void *)&nt,
+                    (void *)&err,  (void *)&wout, (void *)&rin,  (void *)&rout, (void *)&twdf, (void *)&mma};
     return cudaLaunchKernel(a.ks->pipe[which], dim3(grid), dim3(a.ks->pipe_threads), args,
                             (size_t)a.ks->pipe_smem, s);
 }
@@ -861,7 +870,6 @@ int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch,
         if (!factor_ok(n[i])) return AFFT_ERR_SIZE;
     if (kind == AFFT_R2C && n[2] % 2 != 0) return AFFT_ERR_R2C_ODD;
     if (batch < 1) return AFFT_ERR_SIZE;
-    if (precision == AFFT_F32_SPLIT) return AFFT_ERR_UNSUPPORTED;
     const int64_t zlen = kind == AFFT_R2C ? n[2] / 2 : n[2];
     // lines longer than one CTA holds are split four-step (n = n_a n_b, both <= kMaxLine);
     // the contiguous axis of an r2c plan is not split
@@ -899,7 +907,8 @@ int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch,
             any_four = true;
             f.na = split_a[a];
             f.nb = split_b[a];
-            f.a.ks = precision == AFFT_F64 ? generic_kernels_f64() : generic_kernels_f32();
+            f.a.ks = precision == AFFT_F64 ? generic_kernels_f64()
+                     : precision == AFFT_F32_SPLIT ? generic_kernels_split() : generic_kernels_f32();
             f.a.tw_base = (int)tm.size();
             build_desc(f.na, f.a.ks, f.a.desc, tm, tl);
             f.wn_base = (int)tm.size();
@@ -940,6 +949,19 @@ int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch,
             const char *base = (const char *)p->d_twdf;
             for (int a = 0; a < 3; ++a) p->ax[a].desc.twdf = base + (size_t)p->ax[a].tw_base * 16;
             p->ax[2].desc.post_df = base + (size_t)p->post_off * 16;
+        }
+    }
+    if (st == AFFT_OK && precision == AFFT_F32_SPLIT) {
+        if (cudaMalloc(&p->d_mma, kSplitTableBytes) != cudaSuccess) {
+            p->d_mma = nullptr;
+            st = AFFT_ERR_NOMEM;
+        } else if (split_fragments(p->d_mma, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+            st = AFFT_ERR_CUDA;
+        } else {
+            for (int a = 0; a < 3; ++a) {
+                p->ax[a].desc.mma = p->d_mma;
+                p->four[a].a.desc.mma = p->d_mma;
+            }
         }
     }
     if (st == AFFT_OK && any_four) {
@@ -1028,13 +1050,14 @@ int afft_plan_destroy(afft_plan *p)
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     int st = AFFT_OK;
-    if (p->d_tw || p->d_work || p->d_err || p->d_four || p->d_twdf) {
+    if (p->d_tw || p->d_work || p->d_err || p->d_four || p->d_twdf || p->d_mma) {
         if (cudaDeviceSynchronize() != cudaSuccess) st = AFFT_ERR_CUDA;
         if (p->d_tw) cudaFree(p->d_tw);
         if (p->d_twdf) cudaFree(p->d_twdf);
         if (p->d_work) cudaFree(p->d_work);
         if (p->d_err) cudaFree(p->d_err);
         if (p->d_four) cudaFree(p->d_four);
+        if (p->d_mma) cudaFree(p->d_mma);
     }
     for (cudaEvent_t ev : p->events) cudaEventDestroy(ev);
     for (cudaEvent_t ev : p->chunk_ev) cudaEventDestroy(ev);
@@ -1216,7 +1239,8 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         "\"pipelined\": [%d, %d], \"contig_lines\": %d, \"strided_lines\": [%d, %d], \"padded_row\": %lld, "
         "\"l2_slab_planes\": %d}",
         (long long)p->n[0], (long long)p->n[1], (long long)p->n[2], (long long)p->batch,
-        p->kind == AFFT_C2C ? "c2c" : "r2c", p->precision == AFFT_F64 ? "f64" : "f32", radix[0], radix[1], radix[2],
+        p->kind == AFFT_C2C ? "c2c" : "r2c",
+        p->precision == AFFT_F64 ? "f64" : p->precision == AFFT_F32_SPLIT ? "f32split" : "f32", radix[0], radix[1], radix[2],
         !p->ax[0].ks->generic, !p->ax[1].ks->generic, !p->ax[2].ks->generic, p->four[0].on, p->four[1].on,
         p->four[2].on, p->ax[0].pipe, p->ax[1].pipe, p->ax[2].launch.lines,
         p->ax[0].pipe ? p->ax[0].ks->pipe_lines : p->ax[0].launch.lines,

@@ -31,6 +31,9 @@ struct StageDesc {
     // or null to compute in FP64 (specialised kernels then use float-float)
     const void *twdf;              // this axis' tables, same offsets as `tw`
     const void *post_df;           // the r2c/c2r table w_{2M}^k
+    // split-precision plans: the tensor-core fragments of the 16-point DFT matrix
+    // (both directions, see fft_split.cuh), else null
+    const unsigned *mma;
 };
 
 // Butterflies a thread carries per pass for radix R: at most 16 complex
@@ -76,8 +79,9 @@ enum { KS_STRIDED_FWD = 0, KS_STRIDED_BWD, KS_CONTIG_FWD, KS_CONTIG_BWD, KS_R2C,
 // Pipelined strided kernels (persistent CTAs, double-buffered tiles), indexed
 // by PIPE_*.  Signature: (const V *in, V *out, CUtensorMap map, const V *tw,
 // long long W, long long tiles_per_outer, long long ntiles, unsigned *err,
-// long long Wout, int remap_in, int remap_out, const void *twdf) (twdf: the
-// float-float twiddles of an FP64 plan, or null); the TMA variants read through
+// long long Wout, int remap_in, int remap_out, const void *twdf, const unsigned
+// *mma) (twdf: the float-float twiddles of an FP64 plan, or null; mma: the
+// tensor-core DFT-16 table of a split-precision plan, or null); the TMA variants read through
 // `map`, the cp.async ones through `in`.  Input column c is stored to output
 // column c (remap_in == 0), or, with q = c / remap_in and k = c % remap_in,
 // to q * remap_out + k when k < remap_out and nowhere otherwise (used to move
@@ -114,5 +118,12 @@ const KernelSet *spec_kernels_f64(int n);
 // Generic kernels (any n whose radix plan the host builds).
 const KernelSet *generic_kernels_f32();
 const KernelSet *generic_kernels_f64();
+// Generic complex64 kernels whose radix-16 passes run on the tensor cores
+// (split-precision plans), and the device table of their DFT-16 fragments
+// (kSplitTableBytes, written by split_fragments on `stream`).
+const KernelSet *generic_kernels_split();
+const KernelSet *spec_kernels_split(int n);
+constexpr size_t kSplitTableBytes = 2 * 32 * 32 * sizeof(unsigned);
+cudaError_t split_fragments(unsigned *table, cudaStream_t stream);
 
 }  // namespace afft

@@ -235,17 +235,43 @@ __device__ __forceinline__ void pair_pass(const float2 *src, const float2 *__res
     }
 }
 
-// The stage's global output for both pass kinds, resolved per thread per tile
+// Output of a tile's column l (tile columns start at c0), for passes whose
+// threads do not own fixed columns (the tensor-core radix-16 pass): column
+// c = c0 + l goes to c (remap_in == 0) or to q remap_out + k (c = q remap_in
+// + k, k < remap_out), and nowhere past the array's W columns.
+template <typename V> struct PipeColOut {
+    V *base;                          // &y[o][0][0]
+    long long Wout, c0, W;
+    int remap_in, remap_out;
+    __device__ __forceinline__ void operator()(int l, int p, V v) const
+    {
+        long long c = c0 + l;
+        if (c >= W) return;
+        if (remap_in > 0) {
+            const long long q = c / remap_in, k = c - q * remap_in;
+            if (k >= remap_out) return;
+            c = q * remap_out + k;
+        }
+        base[(long long)p * Wout + c] = v;
+    }
+};
+
+// The stage's global output for the pass kinds, resolved per thread per tile
 // (stored as V, computed as CT).
 template <typename V, typename CT = V> struct TileOut {
     GlobalColRemapOut<V, CT> single;  // one column per thread
     PairGlobalOut pair;               // two columns per thread (float2 only)
+    PipeColOut<V> cols;               // any column (split-precision radix-16 passes)
 };
 
 // Passes Seq<R, Rest...>: pass number Q reads buffer X (Q even) or C (Q odd)
-// and writes the other one; the last pass writes the stage's output.
-template <class Sh, int S, int N, int Ns, int TwOff, int Q, typename V, class Out, int R, int... Rest>
-__device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V *tw, const Out &out)
+// and writes the other one; the last pass writes the stage's output.  Split:
+// radix-16 passes of complex64 tiles on the tensor cores (fft_split.cuh, table
+// `mma` of both directions).
+template <class Sh, int S, int N, int Ns, int TwOff, int Q, bool Split = false, typename V, class Out, int R,
+          int... Rest>
+__device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V *tw, const Out &out,
+                                            const unsigned *mma = nullptr)
 {
     constexpr bool Last = sizeof...(Rest) == 0;
     constexpr int LG = Sh::lg, NT = Sh::threads;
@@ -257,16 +283,20 @@ __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V
         else pair_pass<R, S, N, Ns, LG, NT, B>(src, tw + TwOff, PairSmemOut<LG>{dst});
     } else {
         const SmemRowsC<V, LG> in_rows{src};
-        if constexpr (Last)
-            radix_pass<R, S, false, NT>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows, out.single);
+        if constexpr (Last && Split && R == 16)
+            spec_pass<R, S, false, Split, NT>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows, out.cols,
+                                              mma);
+        else if constexpr (Last)
+            spec_pass<R, S, false, Split, NT>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows, out.single,
+                                              mma);
         else
-            radix_pass<R, S, false, NT>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
-                                        SmemRowsC<V, LG>{dst});
+            spec_pass<R, S, false, Split, NT>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                              SmemRowsC<V, LG>{dst}, mma);
     }
     if constexpr (!Last) {
         __syncthreads();
         constexpr int next = TwOff + (Ns > 1 ? Ns * (R - 1) : 0);
-        pipe_passes<Sh, S, N, Ns * R, next, Q + 1>(Seq<Rest...>{}, X, C, tw, out);
+        pipe_passes<Sh, S, N, Ns * R, next, Q + 1, Split>(Seq<Rest...>{}, X, C, tw, out, mma);
     }
 }
 
@@ -289,11 +319,12 @@ __device__ __forceinline__ bool pipe_df(Seq<R0, Rest...>, double2 *X, double2 *C
 
 // ---------------------------------------------------------------- kernel ---
 
-template <class P, int S, typename V, bool TMA>
+template <class P, int S, typename V, bool TMA, bool Split = false>
 __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     k_strided_pipe(const V *__restrict__ in, V *out, const __grid_constant__ CUtensorMap tmap,
                    const V *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
-                   unsigned *err, long long Wout, int remap_in, int remap_out, const void *twdf)
+                   unsigned *err, long long Wout, int remap_in, int remap_out, const void *twdf,
+                   const unsigned *mma)
 {
     using Sh = PipeShape<P, V>;
     constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
@@ -367,6 +398,7 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
         const long long c0 = (t - o * tiles_per_outer) * LINES;
         TileOut<V> to;
         to.single = GlobalColRemapOut<V>{out + o * (long long)N * Wout, Wout, out_col(c0 + (tid & (LINES - 1)))};
+        to.cols = PipeColOut<V>{out + o * (long long)N * Wout, Wout, c0, W, remap_in, remap_out};
         if constexpr (sizeof(V) == 8) {
             const int lp = tid % (LINES / 2 > 0 ? LINES / 2 : 1);
             const long long a = out_col(c0 + 2 * lp), bcol = out_col(c0 + 2 * lp + 1);
@@ -383,7 +415,7 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
                 done = pipe_df<Sh, S, N>(typename P::seq{}, buf0 + b * TILE, scratch, (const dcx *)twdf, tdf);
             }
         }
-        if (!done) pipe_passes<Sh, S, N, 1, 0, 0>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to);
+        if (!done) pipe_passes<Sh, S, N, 1, 0, 0, Split>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to, mma);
         if (tn >= ntiles) break;
         t = tn;
     }
@@ -564,8 +596,8 @@ template <class F, typename V> KernelSet kernel_set(int n, int npass, const int 
     k.max_threads = F::template threads<V>();
     k.generic = F::generic;
     if constexpr (F::generic) {
-        k.four[0] = (const void *)k_fourstep<-1, V>;
-        k.four[1] = (const void *)k_fourstep<+1, V>;
+        k.four[0] = (const void *)k_fourstep<-1, V, F::split>;
+        k.four[1] = (const void *)k_fourstep<+1, V, F::split>;
         k.poisson_mult = (const void *)k_poisson_mult<V>;
     }
     if constexpr (!F::generic) {
@@ -574,12 +606,14 @@ template <class F, typename V> KernelSet kernel_set(int n, int npass, const int 
         if constexpr (F::plan::npass > 0 && F::plan::n < 1024) {
             using P = typename F::plan;
             using Sh = PipeShape<P, V>;
-            k.pipe[PIPE_FWD_TMA] = (const void *)k_strided_pipe<P, -1, V, true>;
-            k.pipe[PIPE_FWD_CPASYNC] = (const void *)k_strided_pipe<P, -1, V, false>;
-            k.pipe[PIPE_BWD_TMA] = (const void *)k_strided_pipe<P, +1, V, true>;
-            k.pipe[PIPE_BWD_CPASYNC] = (const void *)k_strided_pipe<P, +1, V, false>;
-            k.poisson[0] = (const void *)k_poisson_pipe<P, V, true>;
-            k.poisson[1] = (const void *)k_poisson_pipe<P, V, false>;
+            k.pipe[PIPE_FWD_TMA] = (const void *)k_strided_pipe<P, -1, V, true, F::split>;
+            k.pipe[PIPE_FWD_CPASYNC] = (const void *)k_strided_pipe<P, -1, V, false, F::split>;
+            k.pipe[PIPE_BWD_TMA] = (const void *)k_strided_pipe<P, +1, V, true, F::split>;
+            k.pipe[PIPE_BWD_CPASYNC] = (const void *)k_strided_pipe<P, +1, V, false, F::split>;
+            if constexpr (!F::split) {   // split plans run the Poisson multiply as its own kernel
+                k.poisson[0] = (const void *)k_poisson_pipe<P, V, true>;
+                k.poisson[1] = (const void *)k_poisson_pipe<P, V, false>;
+            }
             k.pipe_lines = Sh::lines;
             k.pipe_threads = Sh::threads;
             k.pipe_smem = Sh::smem;

@@ -30,6 +30,7 @@
 
 #include "afft_internal.h"
 #include "fft_access.cuh"
+#include "fft_split.cuh"
 
 namespace afft {
 
@@ -110,35 +111,48 @@ template <int N, int... Rs> struct LinePlan {
     using seq = Seq<Rs...>;
 };
 
+// One pass of a specialised sequence: radix_pass, or with Split (complex64
+// split-precision families) the tensor-core radix-16 pass of fft_split.cuh.
+template <int R, int S, bool InPlace, bool Split, int NT = 0, typename V, class Map, class Src, class Dst>
+__device__ __forceinline__ void spec_pass(int n, int Ns, const V *__restrict__ tw, int lines, const Map &map,
+                                          const Src &src, const Dst &dst, const unsigned *mma)
+{
+    if constexpr (Split && R == 16 && std::is_same<V, float2>::value)
+        mma16_pass<S>(n, Ns, tw, lines, map, src, dst, mma + (S < 0 ? 0 : 32 * 32));
+    else
+        radix_pass<R, S, InPlace, NT>(n, Ns, tw, lines, map, src, dst);
+}
+
 // Runs passes Seq<R, Rest...> with Ns = product of the earlier radices and
 // TwOff = the table offset of this pass (the host lays tables out the same
 // way: Ns (R - 1) entries per pass with Ns > 1, in pass order).
-template <int S, bool First, bool LastToSmem, int N, int Ns, int TwOff, typename V, class Map,
+template <int S, bool First, bool LastToSmem, int N, int Ns, int TwOff, bool Split, typename V, class Map,
           class Src, class Sm, class Dst, int R, int... Rest>
 __device__ __forceinline__ void run_passes(Seq<R, Rest...>, const V *tw, int lines, const Map &map,
-                                           const Src &src, const Sm &sm, const Dst &dst)
+                                           const Src &src, const Sm &sm, const Dst &dst, const unsigned *mma)
 {
     constexpr bool Last = sizeof...(Rest) == 0;
     if (!First) __syncthreads();
     if constexpr (First && Last) {
-        if constexpr (LastToSmem) radix_pass<R, S, false>(N, Ns, tw + TwOff, lines, map, src, sm);
-        else radix_pass<R, S, false>(N, Ns, tw + TwOff, lines, map, src, dst);
+        if constexpr (LastToSmem) spec_pass<R, S, false, Split>(N, Ns, tw + TwOff, lines, map, src, sm, mma);
+        else spec_pass<R, S, false, Split>(N, Ns, tw + TwOff, lines, map, src, dst, mma);
     } else if constexpr (First) {
-        radix_pass<R, S, false>(N, Ns, tw + TwOff, lines, map, src, sm);
+        spec_pass<R, S, false, Split>(N, Ns, tw + TwOff, lines, map, src, sm, mma);
     } else if constexpr (Last && !LastToSmem) {
-        radix_pass<R, S, false>(N, Ns, tw + TwOff, lines, map, sm, dst);
+        spec_pass<R, S, false, Split>(N, Ns, tw + TwOff, lines, map, sm, dst, mma);
     } else {
-        radix_pass<R, S, true>(N, Ns, tw + TwOff, lines, map, sm, sm);
+        spec_pass<R, S, true, Split>(N, Ns, tw + TwOff, lines, map, sm, sm, mma);
     }
     if constexpr (!Last) {
         constexpr int next = TwOff + (Ns > 1 ? Ns * (R - 1) : 0);
-        run_passes<S, false, LastToSmem, N, Ns * R, next>(Seq<Rest...>{}, tw, lines, map, src, sm, dst);
+        run_passes<S, false, LastToSmem, N, Ns * R, next, Split>(Seq<Rest...>{}, tw, lines, map, src, sm, dst, mma);
     }
 }
 
-template <class P, int S, bool LastToSmem, typename V, class Map, class Src, class Sm, class Dst>
+template <class P, int S, bool LastToSmem, bool Split = false, typename V, class Map, class Src, class Sm,
+          class Dst>
 __device__ __forceinline__ void run_plan(const V *tw, int lines, const Map &map, const Src &src,
-                                         const Sm &sm, const Dst &dst)
+                                         const Sm &sm, const Dst &dst, const unsigned *mma = nullptr)
 {
     if constexpr (P::npass == 0) {  // n == 1: a copy
         for (int idx = threadIdx.x; idx < lines; idx += blockDim.x) {
@@ -146,7 +160,7 @@ __device__ __forceinline__ void run_plan(const V *tw, int lines, const Map &map,
             else dst(idx, 0, src(idx, 0));
         }
     } else {
-        run_passes<S, true, LastToSmem, P::n, 1, 0>(typename P::seq{}, tw, lines, map, src, sm, dst);
+        run_passes<S, true, LastToSmem, P::n, 1, 0, Split>(typename P::seq{}, tw, lines, map, src, sm, dst, mma);
     }
 }
 
@@ -163,7 +177,7 @@ __device__ __forceinline__ bool df_stage_impl(Seq<R0, Rest...>, const CT *tw, in
 {
     radix_pass<R0, S, false>(P::n, 1, tw, lines, map, src, sm);
     if (!df_tile_ok(bad)) return false;
-    run_passes<S, false, LastToSmem, P::n, R0, 0>(Seq<Rest...>{}, tw, lines, map, sm, sm, dst);
+    run_passes<S, false, LastToSmem, P::n, R0, 0, false>(Seq<Rest...>{}, tw, lines, map, sm, sm, dst, nullptr);
     return true;
 }
 template <class P, int S, bool LastToSmem, typename CT, class Map, class Src, class Sm, class Dst>
@@ -194,12 +208,31 @@ __device__ __noinline__ void smem_pass(V *sm, int n, int Ns, const V *tw, int li
     }
 }
 
-template <int S, bool Rows, typename V>
+// Split-precision radix-16 pass (tensor cores, see fft_split.cuh) on the tile.
+template <int S, bool Rows>
+__device__ __noinline__ void smem_mma16(float2 *sm, int n, int Ns, const float2 *tw, int lines, int log2_lines,
+                                        const unsigned *frag)
+{
+    if constexpr (Rows) {
+        const SmemRows<float2> t{sm, log2_lines};
+        mma16_pass<S>(n, Ns, tw, lines, MapLineFast{log2_lines}, t, t, frag);
+    } else {
+        const SmemLines<float2> t{sm, n};
+        mma16_pass<S>(n, Ns, tw, lines, MapButterflyFast{}, t, t, frag);
+    }
+}
+
+template <int S, bool Rows, bool Split, typename V>
 __device__ __forceinline__ void smem_pass_any(int R, V *sm, int n, int Ns, const V *tw, int lines,
-                                              int log2_lines)
+                                              int log2_lines, const unsigned *mma)
 {
     switch (R) {
-    case 16: smem_pass<16, S, Rows>(sm, n, Ns, tw, lines, log2_lines); break;
+    case 16:
+        if constexpr (Split && std::is_same<V, float2>::value)
+            smem_mma16<S, Rows>(sm, n, Ns, tw, lines, log2_lines, mma + (S < 0 ? 0 : 32 * 32));
+        else
+            smem_pass<16, S, Rows>(sm, n, Ns, tw, lines, log2_lines);
+        break;
     case 8: smem_pass<8, S, Rows>(sm, n, Ns, tw, lines, log2_lines); break;
     case 4: smem_pass<4, S, Rows>(sm, n, Ns, tw, lines, log2_lines); break;
     case 2: smem_pass<2, S, Rows>(sm, n, Ns, tw, lines, log2_lines); break;
@@ -210,8 +243,8 @@ __device__ __forceinline__ void smem_pass_any(int R, V *sm, int n, int Ns, const
 }
 
 // Generic stage body: load src -> smem, all passes in smem, store smem -> dst
-// (skipped with LastToSmem).
-template <int S, bool Rows, bool LastToSmem, typename V, class Map, class Src, class Dst>
+// (skipped with LastToSmem).  Split: radix-16 passes on the tensor cores.
+template <int S, bool Rows, bool LastToSmem, bool Split = false, typename V, class Map, class Src, class Dst>
 __device__ __forceinline__ void run_generic(const StageDesc &d, const V *tw, V *sm, int lines,
                                             int log2_lines, const Map &map, const Src &src,
                                             const Dst &dst)
@@ -228,7 +261,7 @@ __device__ __forceinline__ void run_generic(const StageDesc &d, const V *tw, V *
     }
     for (int p = 0; p < d.npass; ++p) {
         __syncthreads();
-        smem_pass_any<S, Rows>(d.radix[p], sm, n, d.ns[p], tw + d.tw_off[p], lines, log2_lines);
+        smem_pass_any<S, Rows, Split>(d.radix[p], sm, n, d.ns[p], tw + d.tw_off[p], lines, log2_lines, d.mma);
     }
     if constexpr (LastToSmem) return;
     __syncthreads();
@@ -249,14 +282,25 @@ template <typename V> struct SpecThreads;
 template <> struct SpecThreads<float2> { static constexpr int value = 512; };
 template <> struct SpecThreads<double2> { static constexpr int value = 256; };
 
-template <class Plan> struct Spec {
+template <class Plan, bool Split = false> struct Spec {
     static constexpr bool generic = false;
+    static constexpr bool split = Split;
     using plan = Plan;
     template <typename V> static constexpr int threads() { return SpecThreads<V>::value; }
-    static constexpr int min_blocks = 2;
+    static constexpr int min_blocks = Split ? 1 : 2;   // split: the DFT-16 fragments need 128 registers
 };
 struct Generic {
     static constexpr bool generic = true;
+    static constexpr bool split = false;
+    using plan = LinePlan<0>;
+    template <typename V> static constexpr int threads() { return 256; }
+    static constexpr int min_blocks = 1;
+};
+// Generic complex64 kernels of split-precision plans: radix-16 passes on the
+// tensor cores, otherwise as Generic.
+struct GenericSplit {
+    static constexpr bool generic = true;
+    static constexpr bool split = true;
     using plan = LinePlan<0>;
     template <typename V> static constexpr int threads() { return 256; }
     static constexpr int min_blocks = 1;
@@ -283,7 +327,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     const GlobalColsOut<V> dst{out + off, W, valid};
     const MapLineFast map{log2_lines};
     if constexpr (F::generic) {
-        run_generic<S, true, false>(d, tw, sm, lines, log2_lines, map, src, dst);
+        run_generic<S, true, false, F::split>(d, tw, sm, lines, log2_lines, map, src, dst);
     } else {
         if constexpr (UseDf<F, V>::value) {
             if (d.twdf) {
@@ -295,7 +339,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
             }
         }
         const SmemRows<V> tile{sm, log2_lines};
-        run_plan<typename F::plan, S, false>(tw, lines, map, src, tile, dst);
+        run_plan<typename F::plan, S, false, F::split>(tw, lines, map, src, tile, dst, d.mma);
     }
 }
 
@@ -314,7 +358,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     const GlobalLinesOut<V> dst{out + b0 * n, n, valid, scale};
     const MapButterflyFast map{};
     if constexpr (F::generic) {
-        run_generic<S, false, false>(d, tw, sm, lines, 0, map, src, dst);
+        run_generic<S, false, false, F::split>(d, tw, sm, lines, 0, map, src, dst);
     } else {
         if constexpr (UseDf<F, V>::value) {
             if (d.twdf) {
@@ -326,7 +370,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
             }
         }
         const SmemLines<V> tile{sm, n};
-        run_plan<typename F::plan, S, false>(tw, lines, map, src, tile, dst);
+        run_plan<typename F::plan, S, false, F::split>(tw, lines, map, src, tile, dst, d.mma);
     }
 }
 
@@ -384,8 +428,8 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
             }
         }
     }
-    if constexpr (F::generic) run_generic<-1, false, true>(d, tw, sm, lines, 0, map, src, tile);
-    else run_plan<typename F::plan, -1, true>(tw, lines, map, src, tile, tile);
+    if constexpr (F::generic) run_generic<-1, false, true, F::split>(d, tw, sm, lines, 0, map, src, tile);
+    else run_plan<typename F::plan, -1, true, F::split>(tw, lines, map, src, tile, tile, d.mma);
     __syncthreads();
     r2c_post<V, V>(tile, o, post_tw, M, ld, valid);
     (void)sizeof(T);
@@ -410,7 +454,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     const GlobalLinesOut<V> dst{reinterpret_cast<V *>(out) + b0 * M, M, valid, scale};
     const MapButterflyFast map{};
     if constexpr (F::generic) {
-        run_generic<+1, false, false>(d, tw, sm, lines, 0, map, src, dst);
+        run_generic<+1, false, false, F::split>(d, tw, sm, lines, 0, map, src, dst);
     } else {
         if constexpr (UseDf<F, V>::value) {
             if (d.twdf) {
@@ -422,7 +466,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
             }
         }
         const SmemLines<V> tile{sm, M};
-        run_plan<typename F::plan, +1, false>(tw, lines, map, src, tile, dst);
+        run_plan<typename F::plan, +1, false, F::split>(tw, lines, map, src, tile, dst, d.mma);
     }
 }
 
@@ -430,7 +474,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
 // [outer * n_b][n_a][W] (row k_b of each outer line group holds the length-n_b
 // DFT outputs, laid out as n_a rows), the output [outer][n_a n_b][W].  Generic
 // family only: the split serves lines longer than one CTA holds.
-template <int S, typename V>
+template <int S, typename V, bool Split>
 __global__ void __launch_bounds__(256, 1)
     k_fourstep(const V *__restrict__ in, V *out, const __grid_constant__ StageDesc d, const V *__restrict__ tw,
                const V *__restrict__ wn, long long W, long long tiles_per_outer, int log2_lines, int nb,
@@ -447,7 +491,7 @@ __global__ void __launch_bounds__(256, 1)
     const int valid = (int)min((long long)lines, W - c0);
     const FourStepSrc<S, V> src{in + op * (long long)na * W + c0, W, valid, wn, kb};
     const FourStepDst<V> dst{out + (o * (long long)na * nb + kb) * W + c0, (long long)nb * W, valid, scale};
-    run_generic<S, true, false>(d, tw, sm, lines, log2_lines, MapLineFast{log2_lines}, src, dst);
+    run_generic<S, true, false, Split>(d, tw, sm, lines, log2_lines, MapLineFast{log2_lines}, src, dst);
 }
 
 // Spectral Poisson multiply on a half spectrum [planes][n1][nhp] (planes =
@@ -472,10 +516,16 @@ __global__ void k_poisson_mult(V *x, long long planes, int n0, int n1, int nhp, 
 }
 
 // Line lengths with specialised kernels and their radix sequences (n first,
-// then the radices in pass order).
+// then the radices in pass order).  Split-precision plans use the sequences of
+// AFFT_SPLIT_LINE_PLANS (as many radix-16 passes as the length allows), and
+// the FP32 kernels for the other lengths of AFFT_LINE_PLANS (no radix-16 pass).
 #define AFFT_LINE_PLANS(X)                                                                          \
     X(1) X(2, 2) X(4, 4) X(8, 8) X(16, 16) X(24, 8, 3) X(32, 8, 4) X(48, 16, 3) X(60, 4, 3, 5)     \
     X(64, 8, 8) X(80, 16, 5) X(96, 8, 4, 3) X(120, 8, 3, 5) X(128, 16, 8) X(160, 8, 4, 5)           \
     X(192, 8, 8, 3) X(256, 16, 16) X(384, 16, 8, 3) X(512, 8, 8, 8) X(1024, 16, 8, 8)
+#define AFFT_SPLIT_LINE_PLANS(X)                                                                    \
+    X(16, 16) X(32, 16, 2) X(48, 16, 3) X(64, 16, 4) X(80, 16, 5) X(96, 16, 3, 2) X(128, 16, 8)     \
+    X(160, 16, 5, 2) X(192, 16, 4, 3) X(256, 16, 16) X(384, 16, 8, 3) X(512, 16, 16, 2)             \
+    X(1024, 16, 16, 4)
 
 }  // namespace afft

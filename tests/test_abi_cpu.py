@@ -52,7 +52,8 @@ def _create(lib, n, kind, prec):
     ((8, 8, 9), 1, 0, 3),        # r2c with odd n2
     ((8, 8, 8), 5, 0, 4),        # kind
     ((8, 8, 8), 0, 7, 5),        # precision
-    ((8, 8, 8), 0, 2, 9),        # split precision: not in this version
+    ((8, 8, 7), 0, 2, 2),        # split precision: same size rules
+    ((8, 8, 9), 1, 2, 3),        # split precision: r2c with odd n2
     ((8, 8, 3 ** 15), 0, 0, 9),  # no split into two factors <= 4096
     ((8, 8, 16384), 1, 1, 9),    # r2c half length 8192
 ])
