@@ -396,6 +396,14 @@ int plan_shapes(afft_plan *p)
 
 // --------------------------------------------------------------- execute ---
 
+// Shared memory of the c2r kernel: the work tile, then (specialised complex128
+// kernels) the tile's half spectra staged at M + 1 elements per line.
+size_t c2r_smem(const AxisPlan &a, size_t elem)
+{
+    if (a.ks->generic || elem != 16) return a.launch.smem;
+    return a.launch.smem + (size_t)a.launch.lines * (a.desc.n + 1) * elem;
+}
+
 cudaError_t launch(const AxisPlan &a, int which, long long blocks, void **args, cudaStream_t s)
 {
     const Launch &L = a.launch;
@@ -543,7 +551,10 @@ cudaError_t c2r(const AxisPlan &a, const V *in, T *out, const V *tw, const V *po
     T sc = (T)scale;
     void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&tw, (void *)&post, (void *)&nlines,
                     (void *)&lines, (void *)&sc};
-    return launch(a, KS_C2R, line_blocks(a, nlines), args, s);
+    const long long blocks = line_blocks(a, nlines);
+    if (blocks <= 0) return cudaSuccess;
+    return cudaLaunchKernel(a.ks->fn[KS_C2R], dim3((unsigned)blocks), dim3(a.launch.threads), args,
+                            c2r_smem(a, sizeof(V)), s);
 }
 
 // Records the timing event `i` (0..3) of the current record, if timing is on.

@@ -10,6 +10,28 @@
 
 namespace afft {
 
+// Shared-memory address and per-thread asynchronous global -> shared copies
+// (cp.async; a zero-byte source fills the destination with zeros).
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill(void *dst, const void *src, bool valid)
+{
+    static_assert(BYTES == 8 || BYTES == 16, "cp.async size");
+    const int n = valid ? BYTES : 0;
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // CTA-wide decision after a float-float first pass: keep float-float only if no
 // value of the tile was too large and some value was >= 2^-50 (two votes, so
 // every thread of the CTA must call it).

@@ -32,11 +32,6 @@
 
 namespace afft {
 
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -94,20 +89,6 @@ __device__ __forceinline__ void fence_async_shared()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <int BYTES>
-__device__ __forceinline__ void cp_async_zfill(void *dst, const void *src, bool valid)
-{
-    static_assert(BYTES == 8 || BYTES == 16, "cp.async size");
-    const int n = valid ? BYTES : 0;
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n)
-                     : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n)
-                     : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Shared-memory rows of a compile-time width: [N][1 << LG].
 template <typename V, int LG> struct SmemRowsC {
@@ -144,9 +125,20 @@ template <class P, typename V> struct PipeShape {
     static constexpr int lines = lines_for(row_lines);
     static constexpr int lg = lines == 16 ? 4 : lines == 8 ? 3 : lines == 4 ? 2 : lines == 2 ? 1 : 0;
     __host__ __device__ static constexpr bool pairs(int r) { return sizeof(V) == 8 && lines >= 2 && 2 * r <= 16; }
-    __host__ __device__ static constexpr int per_thread(int r)   // butterflies (or butterfly pairs) per thread
+    template <int... Rs> __host__ __device__ static constexpr int max_radix(Seq<Rs...>)
     {
-        return pairs(r) ? (16 / (2 * r) > 0 ? 16 / (2 * r) : 1) : bmax_for_radix(r);
+        int m = 1;
+        for (int r : {Rs...}) m = r > m ? r : m;
+        return m;
+    }
+    // butterflies (or butterfly pairs) per thread; complex128 tiles (float-float arithmetic, twice
+    // the registers per value) of plans without a radix-16 pass carry at most 8 values per thread,
+    // for more warps per SM
+    __host__ __device__ static constexpr int per_thread(int r)
+    {
+        return pairs(r) ? (16 / (2 * r) > 0 ? 16 / (2 * r) : 1)
+               : (sizeof(V) == 16 && max_radix(typename P::seq{}) <= 8) ? (8 / r > 1 ? 8 / r : 1)
+                                                                      : bmax_for_radix(r);
     }
     __host__ __device__ static constexpr int units(int r) { return (pairs(r) ? lines / 2 : lines) * (P::n / r); }
     template <int... Rs> __host__ __device__ static constexpr int threads_for(Seq<Rs...>)
@@ -283,15 +275,16 @@ __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V
         else pair_pass<R, S, N, Ns, LG, NT, B>(src, tw + TwOff, PairSmemOut<LG>{dst});
     } else {
         const SmemRowsC<V, LG> in_rows{src};
+        constexpr int B = Sh::per_thread(R);
         if constexpr (Last && Split && R == 16)
-            spec_pass<R, S, false, Split, NT>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows, out.cols,
-                                              mma);
+            spec_pass<R, S, false, Split, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                                 out.cols, mma);
         else if constexpr (Last)
-            spec_pass<R, S, false, Split, NT>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows, out.single,
-                                              mma);
+            spec_pass<R, S, false, Split, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                                 out.single, mma);
         else
-            spec_pass<R, S, false, Split, NT>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
-                                              SmemRowsC<V, LG>{dst}, mma);
+            spec_pass<R, S, false, Split, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                                 SmemRowsC<V, LG>{dst}, mma);
     }
     if constexpr (!Last) {
         __syncthreads();
@@ -310,7 +303,7 @@ __device__ __forceinline__ bool pipe_df(Seq<R0, Rest...>, double2 *X, double2 *C
     constexpr int LG = Sh::lg, NT = Sh::threads;
     DfFlags bad;
     const SmemRowsConvIn<double2, dcx, LG> src{X, &bad};
-    radix_pass<R0, S, false, NT>(N, 1, tw, Sh::lines, MapLineFastC<LG>{}, src,
+    radix_pass<R0, S, false, NT, Sh::per_thread(R0)>(N, 1, tw, Sh::lines, MapLineFastC<LG>{}, src,
                                  SmemRowsC<dcx, LG>{reinterpret_cast<dcx *>(C)});
     if (!df_tile_ok(bad)) return false;
     pipe_passes<Sh, S, N, R0, 0, 1>(Seq<Rest...>{}, reinterpret_cast<dcx *>(X), reinterpret_cast<dcx *>(C), tw, out);

@@ -58,11 +58,11 @@ struct MapButterflyFast {  // contiguous stage: consecutive threads walk along a
 // InPlace the pass reads everything into registers, waits for the whole CTA,
 // then writes.
 
-template <int R, int S, bool InPlace, int NT = 0, typename V, class Map, class Src, class Dst>
+template <int R, int S, bool InPlace, int NT = 0, int BM = 0, typename V, class Map, class Src, class Dst>
 __device__ __forceinline__ void radix_pass(int n, int Ns, const V *__restrict__ tw, int lines,
                                            const Map &map, const Src &src, const Dst &dst)
 {
-    constexpr int B = bmax_for_radix(R);
+    constexpr int B = BM > 0 ? BM : bmax_for_radix(R);   // BM: fewer butterflies per thread (larger CTAs)
     const int nthr = NT > 0 ? NT : (int)blockDim.x;  // NT: compile-time CTA size, when known
     const int nb = n / R;
     const int total = lines * nb;
@@ -113,14 +113,15 @@ template <int N, int... Rs> struct LinePlan {
 
 // One pass of a specialised sequence: radix_pass, or with Split (complex64
 // split-precision families) the tensor-core radix-16 pass of fft_split.cuh.
-template <int R, int S, bool InPlace, bool Split, int NT = 0, typename V, class Map, class Src, class Dst>
+template <int R, int S, bool InPlace, bool Split, int NT = 0, int BM = 0, typename V, class Map, class Src,
+          class Dst>
 __device__ __forceinline__ void spec_pass(int n, int Ns, const V *__restrict__ tw, int lines, const Map &map,
                                           const Src &src, const Dst &dst, const unsigned *mma)
 {
     if constexpr (Split && R == 16 && std::is_same<V, float2>::value)
         mma16_pass<S>(n, Ns, tw, lines, map, src, dst, mma + (S < 0 ? 0 : 32 * 32));
     else
-        radix_pass<R, S, InPlace, NT>(n, Ns, tw, lines, map, src, dst);
+        radix_pass<R, S, InPlace, NT, BM>(n, Ns, tw, lines, map, src, dst);
 }
 
 // Runs passes Seq<R, Rest...> with Ns = product of the earlier radices and
@@ -378,20 +379,27 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
 // line (compute type CT, stored as V):
 //   X[k] = E[k] + w_{2M}^k O[k],  E = (Z[k] + conj Z[M-k]) / 2,
 //   O = (Z[k] - conj Z[M-k]) / (2i),  Z[M] = Z[0].
+// Bins k and M - k share E and O up to conjugation (E[M-k] = conj E[k],
+// O[M-k] = conj O[k], w_{2M}^{M-k} = -conj w_{2M}^k), so one thread reads
+// Z[k] and Z[M-k] once and writes X[k] = E + t and X[M-k] = conj(E - t) with
+// t = w_{2M}^k O[k]; k = 0 gives X[0] and X[M].
 template <typename V, typename CT, class Tile>
 __device__ __forceinline__ void r2c_post(const Tile &tile, V *o, const CT *post_tw, int M, int ld, int valid)
 {
     using T = typename RealOf<CT>::T;
-    const int per = M + 1;
-    for (int idx = threadIdx.x; idx < valid * per; idx += blockDim.x) {
-        const int l = idx / per;
-        const int k = idx - l * per;
-        const CT zk = tile(l, k == M ? 0 : k);
+    const int half = M / 2 + 1;
+    for (int idx = threadIdx.x; idx < valid * half; idx += blockDim.x) {
+        const int l = idx / half;
+        const int k = idx - l * half;
+        const CT zk = tile(l, k);
         const CT zm = cconj(tile(l, k == 0 ? 0 : M - k));
         const CT e = cscale(cadd(zk, zm), T(0.5));
         const CT dd = csub(zk, zm);
         const CT od = cmk<CT>(T(0.5) * dd.y, T(-0.5) * dd.x);  // (zk - zm) / (2i)
-        o[l * ld + k] = Conv<CT, V>::out(cnorm(cadd(e, cmul(od, ldgc(post_tw + k)))));
+        const CT t = cmul(od, ldgc(post_tw + k));
+        V *line = o + l * ld;
+        line[k] = Conv<CT, V>::out(cnorm(cadd(e, t)));
+        if (2 * k != M) line[k == 0 ? M : M - k] = Conv<CT, V>::out(cnorm(cconj(csub(e, t))));
     }
 }
 
@@ -456,17 +464,38 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     if constexpr (F::generic) {
         run_generic<+1, false, false, F::split>(d, tw, sm, lines, 0, map, src, dst);
     } else {
+        // complex128: the tile's half spectra are staged with cp.async behind the work tile (the
+        // host adds lines * (M + 1) elements to the launch's shared memory), so the float-float
+        // first pass reads shared memory; complex64 reads them from global memory in the first
+        // pass (measured faster: the loads overlap the arithmetic)
+        constexpr bool kStage = sizeof(V) == 16;
+        constexpr int kRow = 128 / (int)sizeof(V);
+        V *xs = sm + (lines * M + kRow - 1) / kRow * kRow;
+        if constexpr (kStage) {
+            const V *xin = in + b0 * ld;
+            const int per = M + 1;
+            for (int idx = threadIdx.x; idx < valid * per; idx += blockDim.x) {
+                const int l = idx / per;
+                cp_async_zfill<(int)sizeof(V)>(xs + idx, xin + (long long)l * ld + (idx - l * per), true);
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+        }
+        const V *xsrc = kStage ? xs : in + b0 * ld;
+        const int xld = kStage ? M + 1 : ld;
         if constexpr (UseDf<F, V>::value) {
             if (d.twdf) {
                 DfFlags bad;
-                const C2RPre<V, dcx> sdf{in + b0 * ld, (const dcx *)d.post_df, M, ld, valid, &bad};
+                const C2RPre<V, dcx> sdf{xsrc, (const dcx *)d.post_df, M, xld, valid, &bad};
                 const GlobalLinesOut<V, dcx> ddf{reinterpret_cast<V *>(out) + b0 * M, M, valid, dfl(scale)};
                 const SmemLines<dcx> tdf{reinterpret_cast<dcx *>(sm), M};
                 if (df_stage<typename F::plan, +1, false>((const dcx *)d.twdf, lines, map, sdf, tdf, ddf, bad)) return;
             }
         }
         const SmemLines<V> tile{sm, M};
-        run_plan<typename F::plan, +1, false, F::split>(tw, lines, map, src, tile, dst, d.mma);
+        const C2RPre<V> sx{xsrc, post_tw, M, xld, valid};
+        run_plan<typename F::plan, +1, false, F::split>(tw, lines, map, sx, tile, dst, d.mma);
     }
 }
 
@@ -519,10 +548,14 @@ __global__ void k_poisson_mult(V *x, long long planes, int n0, int n1, int nhp, 
 // then the radices in pass order).  Split-precision plans use the sequences of
 // AFFT_SPLIT_LINE_PLANS (as many radix-16 passes as the length allows), and
 // the FP32 kernels for the other lengths of AFFT_LINE_PLANS (no radix-16 pass).
-#define AFFT_LINE_PLANS(X)                                                                          \
-    X(1) X(2, 2) X(4, 4) X(8, 8) X(16, 16) X(24, 8, 3) X(32, 8, 4) X(48, 16, 3) X(60, 4, 3, 5)     \
-    X(64, 8, 8) X(80, 16, 5) X(96, 8, 4, 3) X(120, 8, 3, 5) X(128, 16, 8) X(160, 8, 4, 5)           \
-    X(192, 8, 8, 3) X(256, 16, 16) X(384, 16, 8, 3) X(512, 8, 8, 8) X(1024, 16, 8, 8)
+// (Groups A-D only split the complex128 instantiations over translation units
+// that compile in parallel.)
+#define AFFT_LINE_PLANS_A(X)                                                                        \
+    X(1) X(2, 2) X(4, 4) X(8, 8) X(16, 16) X(24, 8, 3) X(32, 8, 4) X(48, 16, 3) X(60, 4, 3, 5) X(64, 8, 8)
+#define AFFT_LINE_PLANS_B(X) X(80, 16, 5) X(96, 8, 4, 3) X(120, 8, 3, 5) X(128, 16, 8) X(160, 8, 4, 5) X(192, 8, 8, 3)
+#define AFFT_LINE_PLANS_C(X) X(256, 16, 16) X(384, 16, 8, 3)
+#define AFFT_LINE_PLANS_D(X) X(512, 8, 8, 8) X(1024, 16, 8, 8)
+#define AFFT_LINE_PLANS(X) AFFT_LINE_PLANS_A(X) AFFT_LINE_PLANS_B(X) AFFT_LINE_PLANS_C(X) AFFT_LINE_PLANS_D(X)
 #define AFFT_SPLIT_LINE_PLANS(X)                                                                    \
     X(16, 16) X(32, 16, 2) X(48, 16, 3) X(64, 16, 4) X(80, 16, 5) X(96, 16, 3, 2) X(128, 16, 8)     \
     X(160, 16, 5, 2) X(192, 16, 4, 3) X(256, 16, 16) X(384, 16, 8, 3) X(512, 16, 16, 2)             \

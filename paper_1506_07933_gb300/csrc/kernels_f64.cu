@@ -1,26 +1,18 @@
-// kernels_f64.cu -- instantiates the stage kernels for double2: one specialised
-// family per line length of AFFT_LINE_PLANS, plus the generic family.  (One
-// translation unit per precision, so the two compile in parallel.)
-#include "fft_pipe.cuh"
+// kernels_f64.cu -- the double2 kernel families: the specialised ones (four
+// translation units, kernels_f64_[a-d].cu) and the generic family.
+#include "kernel_tables.cuh"
 
 namespace afft {
 
-namespace {
-template <class P> struct Radices;
-template <int N, int... Rs> struct Radices<LinePlan<N, Rs...>> {
-    static constexpr int value[] = {Rs..., 0};
-};
-}  // namespace
-
-#define AFFT_SPEC_SET(N, ...)                                                                         \
-    kernel_set<Spec<LinePlan<N, ##__VA_ARGS__>>, double2>(N, LinePlan<N, ##__VA_ARGS__>::npass,           \
-                                                       Radices<LinePlan<N, ##__VA_ARGS__>>::value),
+const KernelSet *spec_kernels_f64_a(int n);
+const KernelSet *spec_kernels_f64_b(int n);
+const KernelSet *spec_kernels_f64_c(int n);
+const KernelSet *spec_kernels_f64_d(int n);
 
 const KernelSet *spec_kernels_f64(int n)
 {
-    static const KernelSet table[] = {AFFT_LINE_PLANS(AFFT_SPEC_SET)};
-    for (const KernelSet &k : table)
-        if (k.n == n) return &k;
+    for (auto *f : {spec_kernels_f64_a, spec_kernels_f64_b, spec_kernels_f64_c, spec_kernels_f64_d})
+        if (const KernelSet *k = f(n)) return k;
     return nullptr;
 }
 

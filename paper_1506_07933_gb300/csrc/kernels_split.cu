@@ -2,7 +2,7 @@
 // (radix-16 passes on the tensor cores, fft_split.cuh): one specialised family
 // per length of AFFT_SPLIT_LINE_PLANS plus the generic family, and the table
 // of DFT-16 fragments those passes load.
-#include "fft_pipe.cuh"
+#include "kernel_tables.cuh"
 
 namespace afft {
 
@@ -43,23 +43,12 @@ cudaError_t split_fragments(unsigned *table, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-namespace {
-template <class P> struct Radices;
-template <int N, int... Rs> struct Radices<LinePlan<N, Rs...>> {
-    static constexpr int value[] = {Rs..., 0};
-};
-}  // namespace
-
-#define AFFT_SPLIT_SET(N, ...)                                                                        \
-    kernel_set<Spec<LinePlan<N, ##__VA_ARGS__>, true>, float2>(N, LinePlan<N, ##__VA_ARGS__>::npass,      \
-                                                             Radices<LinePlan<N, ##__VA_ARGS__>>::value),
+#define AFFT_X(N, ...) AFFT_KERNEL_SET(float2, true, N, ##__VA_ARGS__)
 
 const KernelSet *spec_kernels_split(int n)
 {
-    static const KernelSet table[] = {AFFT_SPLIT_LINE_PLANS(AFFT_SPLIT_SET)};
-    for (const KernelSet &k : table)
-        if (k.n == n) return &k;
-    return nullptr;
+    static const KernelSet table[] = {AFFT_SPLIT_LINE_PLANS(AFFT_X)};
+    return find_set(table, n);
 }
 
 const KernelSet *generic_kernels_split()
