@@ -7,14 +7,17 @@ scheduling step:
 
 * polls completion events, records latency (arrival -> solution ready) and
   frees the stream slot;
-* takes the oldest waiting (n, precision) queue first and, while a stream
-  slot is free and the HBM budget (bytes of plans plus buffers the server
-  holds) allows, groups up to a per-size cap of its requests (a power of two)
+* takes the waiting (n, precision) queues smallest work first (or oldest
+  first) and, while a stream slot is free and the HBM budget (bytes of plans
+  plus buffers the server holds) allows, groups up to a per-size cap of its
+  requests (a power of two)
   into one batched solve: one batched plan, one `afft_execute_poisson` on the
   slot's stream.  A batch gathers its members' right-hand sides into the
   plan's contiguous input (a device copy); a single request is solved in
   place from its own buffer;
-* groups of different sizes run on different streams and overlap on the GPU.
+* groups of different sizes run on different streams and overlap on the GPU;
+  small groups go to high-priority streams (their thread blocks are
+  dispatched ahead of a large solve's), large ones to normal-priority ones.
 
 `run_plain` serves the same requests one at a time on one stream with a
 (cached) single plan per size: the plain one-plan-per-request form the
@@ -157,9 +160,15 @@ class PoissonServer:
     """Continuous-batching Poisson server (see the module docstring)."""
 
     def __init__(self, pool: RhsPool, slots: int = 4, hbm_budget: int = None, max_batch_bytes: int = 64 << 20,
-                 max_batch: int = 16):
+                 max_batch: int = 16, policy: str = "sjf", large_bytes: int = 256 << 20):
         self.pool = pool
-        self.slots = [torch.cuda.Stream() for _ in range(slots)]
+        # slots [0, slots/2) are high-priority streams for small groups; the rest take large ones
+        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+        self.n_fast = slots // 2
+        self.slots = [torch.cuda.Stream(priority=hi) for _ in range(self.n_fast)] + \
+                     [torch.cuda.Stream(priority=lo) for _ in range(slots - self.n_fast)]
+        self.policy = policy
+        self.large_bytes = large_bytes
         free, _ = torch.cuda.mem_get_info()
         self.budget = hbm_budget if hbm_budget is not None else int(free * 0.6)
         self.max_batch_bytes = max_batch_bytes
@@ -167,6 +176,14 @@ class PoissonServer:
         self.plans = {}           # (n, prec, B) -> [idle (plan, f, u)]
         self.held = 0             # bytes of plans and buffers the server holds
         self.results = {}
+
+    def _order(self, queue):
+        """Waiting (n, precision) queues in admission order: oldest head first ("fifo"), or
+        smallest group work first, ties by age ("sjf")."""
+        keys = [k for k, q in queue.items() if q]
+        if self.policy == "fifo":
+            return sorted(keys, key=lambda k: queue[k][0].arrival)
+        return sorted(keys, key=lambda k: (k[0] ** 3 * BYTES[k[1]], queue[k][0].arrival))
 
     def _cap(self, n, prec):
         one = n ** 3 * BYTES[prec]
@@ -284,16 +301,23 @@ class PoissonServer:
                     done.append((group, key))
                     del busy[si]
             free_slots = [i for i in range(len(self.slots)) if i not in busy]
-            for _, (n, prec) in sorted((q[0].arrival, k) for k, q in queue.items() if q):
+            for (n, prec) in self._order(queue):
                 if not free_slots:
                     break
                 q = queue[(n, prec)]
                 B = self._batch(n, prec, len(q))
+                large = B * n ** 3 * BYTES[prec] >= self.large_bytes
+                # large groups run on the normal-priority slots only; small ones prefer the
+                # high-priority slots, so their kernels are dispatched ahead of a large one's
+                usable = [i for i in free_slots if i >= self.n_fast] if large else free_slots
+                if not usable:
+                    continue
                 entry = self._take(n, prec, B)
                 if entry is None:
                     continue
                 group = [q.popleft() for _ in range(B)]
-                si = free_slots.pop(0)
+                si = usable[0]
+                free_slots.remove(si)
                 t = time.perf_counter() - t0
                 for r in group:
                     r.start, r.batch = t, B
