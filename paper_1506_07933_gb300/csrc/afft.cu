@@ -29,6 +29,7 @@ struct AxisPlan {
     bool pipe_avail;       // the family has it and it fits this device
     bool pipe;             // in use (the autotuner may switch it off)
     int pipe_slots;        // CTAs resident at once (SMs x CTAs per SM): the persistent grid's cap
+    int rp_slots;          // the same for the row-pair kernel of odd-width rows (0: none)
 };
 
 // Four-step split of one axis whose lines are longer than a CTA holds
@@ -346,13 +347,27 @@ int plan_shapes(afft_plan *p)
         ap.pipe_slots = sms * per_sm;
         ap.pipe_avail = true;
         ap.pipe = true;
+        ap.rp_slots = 0;
+        if (ks->pipe_rp[0] && ks->pipe_smem_rp <= max_smem) {
+            bool ok = true;
+            for (int k = 0; k < 2 && ok; ++k)
+                ok = cudaFuncSetAttribute(ks->pipe_rp[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          ks->pipe_smem_rp) == cudaSuccess;
+            int rs = 0;
+            if (ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rs, ks->pipe_rp[0], ks->pipe_threads,
+                                                                    ks->pipe_smem_rp) == cudaSuccess && rs >= 1)
+                ap.rp_slots = sms * rs;
+            cudaGetLastError();
+        }
     }
-    // FP32 r2c with an odd half-spectrum width: rows of nh complex64 are not 16-byte aligned,
-    // which TMA needs; keep the N2 and N1 stages in a workspace with rows of nh + 1 and let the
-    // (pipelined) N0 stage convert between that and the compact layout.
+    // The half spectrum keeps its compact rows of nh bins in every stage (nhp == nh).  An odd
+    // nh makes complex64 rows 8 (mod 16) bytes long, which single-row TMA boxes cannot address;
+    // the N1 stage then reads row pairs (k_strided_pipe_rp), and the N0 stage sees each
+    // [n1][nh] plane as one row of n1 nh columns, 16-byte aligned for even n1.  (A workspace
+    // padded to nh + 1 columns was measured slower: the N0 stage that converts between the
+    // layouts writes or reads misaligned sectors on one side, 0.243 ms against 0.19 ms on the
+    // 512^3 workload.)
     p->nhp = nh;
-    if (p->kind == AFFT_R2C && elem == 8 && (nh % 2) == 1 && n0 > 1 && p->ax[0].pipe && !p->four[0].on)
-        p->nhp = nh + 1;
     p->ax[2].desc.ld = p->nhp != nh ? (int)p->nhp : 0;
     const long long nhp = p->nhp;
     // Specialised kernels run two CTAs per SM: keep their tiles to half the SM.
@@ -436,6 +451,22 @@ EncodeTiledFn encode_tiled()
 
 // TMA view of a [outer][n][W] complex array as 8-byte elements: dims
 // (W * C/8, n, outer), box (lines * C/8, min(n, 256), 1).
+// TMA view of a [outer][n][W] complex64 array with W odd as row pairs: dims
+// (2W, n/2, outer) 8-byte elements, box (lines + 2, n/2, 1) (k_strided_pipe_rp).
+bool encode_rowpair_map(CUtensorMap *map, const void *base, long long outer, int n, long long W, int lines)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    if ((W % 2) != 1 || (n % 2) != 0 || n / 2 > 256 || ((uintptr_t)base) % 16 != 0 || 2 * W < lines + 2) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)(2 * W), (cuuint64_t)(n / 2), (cuuint64_t)outer};
+    cuuint64_t strides[2] = {(cuuint64_t)(2 * W * 8), (cuuint64_t)((long long)n * W * 8)};
+    cuuint32_t box[3] = {(cuuint32_t)(lines + 2), (cuuint32_t)(n / 2), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool encode_strided_map(CUtensorMap *map, const void *base, long long outer, int n, long long W, size_t C,
                         int lines)
 {
@@ -464,6 +495,23 @@ cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, lo
 {
     alignas(64) CUtensorMap map;
     std::memset(&map, 0, sizeof map);
+    // odd-width complex64 rows: the row-pair kernel when the family has one
+    if (sizeof(V) == 8 && rm.in == 0 && (W % 2) == 1 && a.rp_slots > 0 &&
+        encode_rowpair_map(&map, in, outer, a.desc.n, W, a.ks->pipe_lines)) {
+        tw += a.tw_base;
+        long long tpo = (W + a.ks->pipe_lines - 1) / a.ks->pipe_lines;
+        long long nt = outer * tpo;
+        long long wout = W;
+        int rin = 0, rout = 0;
+        const void *twdf = nullptr;
+        const unsigned *mma = nullptr;
+        const unsigned grid = (unsigned)std::min<long long>(nt, a.rp_slots);
+        void *args[] = {(void *)&in,  (void *)&out,  (void *)&map, (void *)&tw,   (void *)&W,
+                        (void *)&tpo, (void *)&nt,   (void *)&err, (void *)&wout, (void *)&rin,
+                        (void *)&rout, (void *)&twdf, (void *)&mma};
+        return cudaLaunchKernel(a.ks->pipe_rp[backward ? 1 : 0], dim3(grid), dim3(a.ks->pipe_threads), args,
+                                (size_t)a.ks->pipe_smem_rp, s);
+    }
     const bool tma = encode_strided_map(&map, in, outer, a.desc.n, W, sizeof(V), a.ks->pipe_lines);
     const int which = backward ? (tma ? PIPE_BWD_TMA : PIPE_BWD_CPASYNC) : (tma ? PIPE_FWD_TMA : PIPE_FWD_CPASYNC);
     tw += a.tw_base;

@@ -110,6 +110,11 @@ struct KernelSet {
     int pipe_lines;                // columns per tile of the pipelined kernel
     int pipe_threads;              // its (compile-time) CTA size
     int pipe_smem;                 // its dynamic shared memory (two tile buffers)
+    // complex64 families: the pipelined kernels for rows of odd width, read as row pairs
+    // through TMA ([0] forward, [1] backward; same arguments as pipe[], see
+    // k_strided_pipe_rp) and their shared memory; null / 0 elsewhere
+    const void *pipe_rp[2];
+    int pipe_smem_rp;
 };
 
 // Specialised kernels for line length n, or nullptr.

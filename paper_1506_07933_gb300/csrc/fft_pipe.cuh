@@ -156,6 +156,12 @@ template <class P, typename V> struct PipeShape {
     static constexpr int npass = P::npass;
     static constexpr int tile = P::n * lines;                       // complex elements per tile
     static constexpr int smem = 3 * tile * (int)sizeof(V) + 16;     // 3 buffers, then two mbarriers
+    // odd-width complex64 rows read as row pairs (k_strided_pipe_rp): load buffers of two
+    // [n/2][lines + 2] boxes, then the scratch tile and the mbarriers
+    static constexpr int lw = lines + 2;
+    static constexpr int tile_rp = P::n * lw;
+    static constexpr int smem_rp = (2 * tile_rp + tile) * (int)sizeof(V) + 16;
+    static constexpr bool rp_ok = sizeof(V) == 8 && lines == 16 && P::n % 16 == 0 && P::n / 2 <= 256;
     static constexpr int box_rows = tma_box_rows(P::n);
     static_assert((box_rows * lines * (int)sizeof(V)) % 128 == 0 || box_rows == P::n,
                   "TMA boxes must start 128-byte aligned in shared memory");
@@ -414,6 +420,170 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     }
 }
 
+// ----------------------------------------------- odd-width complex64 rows ---
+// A strided stage over rows of W complex64 with W odd (the N1 stage of an r2c
+// plan whose half spectrum has n2/2 + 1 bins, n2/2 even) cannot use TMA on
+// single rows: their pitch, 8 W bytes, is not a multiple of 16.  Two rows
+// are: the array is viewed as [outer][n/2][2W] and a tile of 16 columns c0..
+// of all n rows is two boxes of lines + 2 = 18 columns and n/2 row pairs,
+// A at x = c0 (even rows, column l at offset l) and B at x = W + c0 - 1 (odd
+// rows, column l at offset l + 1); both x are even, as TMA requires.  The
+// first pass reads the rows from the boxes, the others use the 16-wide tiles.
+
+// First-pass source for threads owning one fixed column l.
+template <int LW> struct RowPairIn {
+    const float2 *A, *B;
+    int l;
+    __device__ __forceinline__ float2 operator()(int, int p) const
+    {
+        const int h = p >> 1;
+        return (p & 1) ? B[h * LW + l + 1] : A[h * LW + l];
+    }
+};
+
+// Column-pair first pass (Ns = 1) over the row-pair boxes.
+template <int R, int S, int N, int LW, int LG, int NT, int B, class Dst>
+__device__ __forceinline__ void pair_pass_rp(const float2 *A, const float2 *Bx, const Dst &dst)
+{
+    constexpr int PAIRS = (1 << LG) / 2, NB = N / R, TOTAL = PAIRS * NB;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int idx = threadIdx.x + b * NT;
+        if (B * NT == TOTAL || idx < TOTAL) {
+            const int lp = idx % PAIRS, j = idx / PAIRS;
+            float2 lo[R], hi[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int p = j + r * NB, odd = p & 1;
+                const float2 *row = (odd ? Bx : A) + (p >> 1) * LW + 2 * lp + odd;
+                lo[r] = row[0];
+                hi[r] = row[1];
+            }
+            Dft<R, S, float2>::run(lo);
+            Dft<R, S, float2>::run(hi);
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst(lp, j * R + r, lo[r], hi[r]);   // Ns = 1: output j R + r
+        }
+    }
+}
+
+// Stores of the column-pair passes into rows of odd pitch: a 16-byte store
+// where row p puts the pair on a 16-byte boundary, else two 8-byte stores.
+struct PairGlobalOutOdd {
+    float2 *base;
+    long long W;
+    long long oc0, oc1;            // this thread's two output columns (-1: not stored)
+    bool vec;                      // adjacent columns and a 16-byte aligned base
+    __device__ __forceinline__ void operator()(int, int p, float2 lo, float2 hi) const
+    {
+        const long long e = (long long)p * W;
+        float2 *row = base + e;
+        if (vec && ((e + oc0) & 1) == 0) {
+            *reinterpret_cast<float4 *>(row + oc0) = make_float4(lo.x, lo.y, hi.x, hi.y);
+        } else {
+            if (oc0 >= 0) row[oc0] = lo;
+            if (oc1 >= 0) row[oc1] = hi;
+        }
+    }
+};
+struct TileOutOdd {
+    GlobalColRemapOut<float2> single;
+    PairGlobalOutOdd pair;
+};
+
+// The first pass from the row-pair boxes (into C, or to the output when it is
+// the only pass), then the other passes ping-pong between C and X (Q = 1).
+template <class Sh, int S, int N, class Out, int R0, int... Rest>
+__device__ __forceinline__ void rp_passes(Seq<R0, Rest...>, float2 *X, float2 *C, const float2 *tw, const Out &out,
+                                          int l)
+{
+    constexpr int LG = Sh::lg, NT = Sh::threads, LW = Sh::lw;
+    constexpr bool Last = sizeof...(Rest) == 0;
+    const float2 *A = X, *Bx = X + (N / 2) * LW;
+    if constexpr (Sh::pairs(R0)) {
+        constexpr int B = Sh::per_thread(R0);
+        if constexpr (Last) pair_pass_rp<R0, S, N, LW, LG, NT, B>(A, Bx, out.pair);
+        else pair_pass_rp<R0, S, N, LW, LG, NT, B>(A, Bx, PairSmemOut<LG>{C});
+    } else {
+        constexpr int B = Sh::per_thread(R0);
+        const RowPairIn<LW> in{A, Bx, l};
+        if constexpr (Last)
+            radix_pass<R0, S, false, NT, B>(N, 1, tw, Sh::lines, MapLineFastC<LG>{}, in, out.single);
+        else
+            radix_pass<R0, S, false, NT, B>(N, 1, tw, Sh::lines, MapLineFastC<LG>{}, in, SmemRowsC<float2, LG>{C});
+    }
+    if constexpr (!Last) {
+        __syncthreads();
+        pipe_passes<Sh, S, N, R0, 0, 1>(Seq<Rest...>{}, X, C, tw, out);
+    }
+}
+
+// Persistent, double-buffered strided stage over odd-width complex64 rows (same
+// argument list as k_strided_pipe; the tensor map views [outer][n/2][2W] with
+// boxes of 18 x n/2; no column remap).
+template <class P, int S>
+__global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
+    k_strided_pipe_rp(const float2 *__restrict__, float2 *out, const __grid_constant__ CUtensorMap tmap,
+                      const float2 *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
+                      unsigned *err, long long, int, int, const void *, const unsigned *)
+{
+    using V = float2;
+    using Sh = PipeShape<P, V>;
+    constexpr int N = P::n, LINES = Sh::lines, LW = Sh::lw, TILE_RP = Sh::tile_rp;
+    constexpr unsigned BOX_BYTES = (N / 2) * LW * sizeof(V);
+    static_assert(Sh::rp_ok, "row-pair tiles: 16 complex64 columns, n a multiple of 16, at most 512");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    V *const buf0 = reinterpret_cast<V *>(smem_raw);   // load buffer b at buf0 + b * TILE_RP
+    V *const scratch = buf0 + 2 * TILE_RP;
+    unsigned long long *const bars =
+        reinterpret_cast<unsigned long long *>(smem_raw + (2 * TILE_RP + Sh::tile) * sizeof(V));
+    const int tid = threadIdx.x;
+
+    long long t = blockIdx.x;
+    if (t >= ntiles) return;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](long long tile, int b) {
+        if (tid != 0) return;
+        const long long o = tile / tiles_per_outer;
+        const long long c0 = (tile - o * tiles_per_outer) * LINES;
+        fence_async_shared();
+        mbar_expect_tx(&bars[b], 2 * BOX_BYTES);
+        tma_load_3d(buf0 + b * TILE_RP, &tmap, (int)c0, 0, (int)o, &bars[b]);
+        tma_load_3d(buf0 + b * TILE_RP + (N / 2) * LW, &tmap, (int)(W + c0 - 1), 0, (int)o, &bars[b]);
+    };
+
+    issue(t, 0);
+    for (int i = 0;; ++i) {
+        const int b = i & 1;
+        const bool ok = mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(err, 1u);
+            return;
+        }
+        const long long tn = t + gridDim.x;
+        if (tn < ntiles) issue(tn, b ^ 1);
+
+        const long long o = t / tiles_per_outer;
+        const long long c0 = (t - o * tiles_per_outer) * LINES;
+        const int l = tid & (LINES - 1), lp = tid % (LINES / 2);
+        V *obase = out + o * (long long)N * W;
+        const long long a = c0 + 2 * lp;
+        TileOutOdd to;
+        to.single = GlobalColRemapOut<V>{obase, W, c0 + l < W ? c0 + l : -1};
+        to.pair = PairGlobalOutOdd{obase, W, a < W ? a : -1, a + 1 < W ? a + 1 : -1,
+                                   a + 1 < W && (reinterpret_cast<unsigned long long>(obase) & 15) == 0};
+        rp_passes<Sh, S, N>(typename P::seq{}, buf0 + b * TILE_RP, scratch, tw, to, l);
+        if (tn >= ntiles) break;
+        t = tn;
+    }
+}
+
 // ------------------------------------------------------ Poisson operator ---
 // The spectral Poisson solve -Lap u = f on [0, 2 pi)^3 divides each bin of
 // the r2c spectrum by |k|^2 (integer wavenumbers k_i = m for m <= n_i/2, else
@@ -610,6 +780,11 @@ template <class F, typename V> KernelSet kernel_set(int n, int npass, const int 
             k.pipe_lines = Sh::lines;
             k.pipe_threads = Sh::threads;
             k.pipe_smem = Sh::smem;
+            if constexpr (Sh::rp_ok && !F::split) {
+                k.pipe_rp[0] = (const void *)k_strided_pipe_rp<P, -1>;
+                k.pipe_rp[1] = (const void *)k_strided_pipe_rp<P, +1>;
+                k.pipe_smem_rp = Sh::smem_rp;
+            }
         }
     }
     return k;

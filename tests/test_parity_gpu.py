@@ -138,15 +138,18 @@ def test_ragged_tiles(shape, prec):
            TOL[prec])
 
 
-@pytest.mark.parametrize("shape", [(16, 24, 40), (64, 48, 96), (32, 3, 96), (120, 8, 12), (8, 1, 24)])
-def test_r2c_padded_internal_layout(shape):
-    """FP32 r2c plans whose half-spectrum width n2/2+1 is odd keep the N2/N1 stages in a
-    workspace with an even row pitch and convert in the N0 stage; results must not change."""
+@pytest.mark.parametrize("shape", [(16, 24, 40), (64, 48, 96), (32, 3, 96), (120, 8, 12), (8, 1, 24),
+                                   (8, 512, 512), (4, 256, 64), (6, 48, 36), (2, 32, 8), (3, 16, 120),
+                                   (5, 160, 72), (2, 384, 40)])
+def test_r2c_odd_width_rows(shape):
+    """FP32 r2c plans whose half-spectrum width n2/2+1 is odd: complex64 rows of odd width,
+    read as row pairs through TMA in the N1 stage where n1 allows (a multiple of 16, at most
+    512), by per-element copies otherwise; results must not change."""
     x = synth.uniform_real(shape, 31).astype(np.float32)
     ref = oracle.r2c(x)
-    report("r2c padded %s f32" % (shape,), oracle.rel_l2(gpu_r2c(x, "f32"), ref), TOL["f32"])
+    report("r2c odd rows %s f32" % (shape,), oracle.rel_l2(gpu_r2c(x, "f32"), ref), TOL["f32"])
     H = ref.astype(np.complex64)
-    report("c2r padded %s f32" % (shape,), oracle.rel_l2(gpu_c2r(H, shape, "f32"), oracle.c2r(H, shape[2])),
+    report("c2r odd rows %s f32" % (shape,), oracle.rel_l2(gpu_c2r(H, shape, "f32"), oracle.c2r(H, shape[2])),
            TOL["f32"])
 
 
