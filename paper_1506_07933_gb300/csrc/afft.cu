@@ -48,14 +48,11 @@ struct afft_plan {
     int kind;
     int precision;
     int64_t nh;            // last-axis length of the complex array: n2 (C2C) or n2/2+1 (R2C)
-    int64_t nhp;           // row pitch of the internal R2C layout: nh, or nh + 1 so that rows
-                           // are 16-byte aligned for TMA (then the workspace holds the N2, N1
-                           // stages and the N0 stage converts to/from the compact layout)
     AxisPlan ax[3];        // ax[2] transforms the contiguous axis (length n2, or n2/2 for R2C)
     int post_off;          // R2C: offset of the w_{n2}^k table (n2/2+1 entries)
     void *d_tw;            // twiddle tables (float2 or double2)
     void *d_twdf;          // FP64 plans: the same tables in float-float (16 bytes per entry)
-    void *d_work;          // R2C workspace: n0*n1*nhp complex
+    void *d_work;          // R2C workspace: n0*n1*nh complex (the c2r stages)
     size_t work_bytes;
     int device;
     // per-stage timing (afft_plan_timing_begin / _end)
@@ -66,7 +63,7 @@ struct afft_plan {
     // L2-resident fusion of the N2 and N1 stages: slabs of `chunk_planes` planes,
     // the N1 stage of slab c on a second stream while the N2 stage of slab c+1 runs
     FourStep four[3];      // per axis
-    void *d_four;          // four-step intermediate: n0*n1*nhp complex
+    void *d_four;          // four-step intermediate: n0*n1*nh complex
     unsigned *d_mma;       // split-precision plans: DFT-16 tensor-core fragments
     int contig_target;     // points per CTA of the contiguous stage (0: default)
     size_t chunk_bytes;    // requested slab size (0: off)
@@ -360,16 +357,14 @@ int plan_shapes(afft_plan *p)
             cudaGetLastError();
         }
     }
-    // The half spectrum keeps its compact rows of nh bins in every stage (nhp == nh).  An odd
-    // nh makes complex64 rows 8 (mod 16) bytes long, which single-row TMA boxes cannot address;
-    // the N1 stage then reads row pairs (k_strided_pipe_rp), and the N0 stage sees each
-    // [n1][nh] plane as one row of n1 nh columns, 16-byte aligned for even n1.  (A workspace
-    // padded to nh + 1 columns was measured slower: the N0 stage that converts between the
-    // layouts writes or reads misaligned sectors on one side, 0.243 ms against 0.19 ms on the
-    // 512^3 workload.)
-    p->nhp = nh;
-    p->ax[2].desc.ld = p->nhp != nh ? (int)p->nhp : 0;
-    const long long nhp = p->nhp;
+    // The half spectrum keeps its compact rows of nh bins in every stage.  An odd nh makes
+    // complex64 rows 8 (mod 16) bytes long, which single-row TMA boxes cannot address; the N1
+    // stage then reads row pairs (k_strided_pipe_rp), and the N0 stage sees each [n1][nh]
+    // plane as one row of n1 nh columns, 16-byte aligned for even n1.  (A workspace padded to
+    // nh + 1 columns was measured slower: the N0 stage that converts between the layouts
+    // writes or reads misaligned sectors on one side, 0.243 ms against 0.19 ms on the 512^3
+    // workload.)
+    p->ax[2].desc.ld = 0;
     // Specialised kernels run two CTAs per SM: keep their tiles to half the SM.
     auto budget = [&](const AxisPlan &a) -> size_t {
         return a.ks->generic ? (size_t)max_smem : (size_t)std::min(max_smem, 112 * 1024);
@@ -378,7 +373,7 @@ int plan_shapes(afft_plan *p)
     // width of each axis' lines (W of its [outer][n][W] view); a four-step axis runs
     // its first half with W * n_a
     const long long outer[3] = {B, B * n0, B * n0 * n1};
-    const long long width[3] = {n1 * nh, nhp, 1};
+    const long long width[3] = {n1 * nh, nh, 1};
     for (int a = 0; a < 3; ++a) {
         const FourStep &f = p->four[a];
         AxisPlan &ap = p->ax[a];
@@ -483,32 +478,23 @@ bool encode_strided_map(CUtensorMap *map, const void *base, long long outer, int
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Column remap of a strided stage (see afft_internal.h): remap_in == 0 keeps columns.
-struct Remap {
-    long long Wout;
-    int in, out;
-};
-
 template <typename V>
 cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, long long outer, long long W,
-                         int backward, unsigned *err, const Remap &rm, cudaStream_t s)
+                         int backward, unsigned *err, cudaStream_t s)
 {
     alignas(64) CUtensorMap map;
     std::memset(&map, 0, sizeof map);
     // odd-width complex64 rows: the row-pair kernel when the family has one
-    if (sizeof(V) == 8 && rm.in == 0 && (W % 2) == 1 && a.rp_slots > 0 &&
+    if (sizeof(V) == 8 && (W % 2) == 1 && a.rp_slots > 0 &&
         encode_rowpair_map(&map, in, outer, a.desc.n, W, a.ks->pipe_lines)) {
         tw += a.tw_base;
         long long tpo = (W + a.ks->pipe_lines - 1) / a.ks->pipe_lines;
         long long nt = outer * tpo;
-        long long wout = W;
-        int rin = 0, rout = 0;
         const void *twdf = nullptr;
         const unsigned *mma = nullptr;
         const unsigned grid = (unsigned)std::min<long long>(nt, a.rp_slots);
-        void *args[] = {(void *)&in,  (void *)&out,  (void *)&map, (void *)&tw,   (void *)&W,
-                        (void *)&tpo, (void *)&nt,   (void *)&err, (void *)&wout, (void *)&rin,
-                        (void *)&rout, (void *)&twdf, (void *)&mma};
+        void *args[] = {(void *)&in, (void *)&out, (void *)&map, (void *)&tw,   (void *)&W,
+                        (void *)&tpo, (void *)&nt, (void *)&err, (void *)&twdf, (void *)&mma};
         return cudaLaunchKernel(a.ks->pipe_rp[backward ? 1 : 0], dim3(grid), dim3(a.ks->pipe_threads), args,
                                 (size_t)a.ks->pipe_smem_rp, s);
     }
@@ -517,25 +503,21 @@ cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, lo
     tw += a.tw_base;
     long long tpo = (W + a.ks->pipe_lines - 1) / a.ks->pipe_lines;
     long long nt = outer * tpo;
-    long long wout = rm.in > 0 ? rm.Wout : W;
-    int rin = rm.in, rout = rm.out;
     const void *twdf = a.desc.twdf;
     const unsigned *mma = a.desc.mma;
     const unsigned grid = (unsigned)std::min<long long>(nt, a.pipe_slots);
-    void *args[] = {(void *)&in,   (void *)&out,  (void *)&map,  (void *)&tw,   (void *)&W,    (void *)&tpo, (void *)&nt,
-                    (void *)&err,  (void *)&wout, (void *)&rin,  (void *)&rout, (void *)&twdf, (void *)&mma};
+    void *args[] = {(void *)&in, (void *)&out, (void *)&map, (void *)&tw,   (void *)&W,
+                    (void *)&tpo, (void *)&nt, (void *)&err, (void *)&twdf, (void *)&mma};
     return cudaLaunchKernel(a.ks->pipe[which], dim3(grid), dim3(a.ks->pipe_threads), args,
                             (size_t)a.ks->pipe_smem, s);
 }
 
-// A strided stage over a [outer][n][W] array (in place when in == out).  The
-// column remap needs the pipelined kernel; plans only ask for it then.
+// A strided stage over a [outer][n][W] array (in place when in == out).
 template <typename V>
 cudaError_t strided(const AxisPlan &a, const V *in, V *out, const V *tw, long long outer, long long W,
-                    int backward, cudaStream_t s, unsigned *err, const Remap &rm = Remap{0, 0, 0})
+                    int backward, cudaStream_t s, unsigned *err)
 {
-    if (a.pipe) return strided_pipe<V>(a, in, out, tw, outer, W, backward, err, rm, s);
-    if (rm.in > 0) return cudaErrorInvalidValue;
+    if (a.pipe) return strided_pipe<V>(a, in, out, tw, outer, W, backward, err, s);
     StageDesc d = a.desc;
     tw += a.tw_base;
     long long tpo = (W + a.launch.lines - 1) / a.launch.lines;
@@ -618,19 +600,18 @@ void mark(afft_plan *p, int i, cudaStream_t s)
 // unsplit strided stages are never the scaled last stage).
 template <typename V>
 cudaError_t axis_stage(afft_plan *p, int a, const V *in, V *out, long long outer, long long W, int backward,
-                       double scale, cudaStream_t s, const Remap &rm = Remap{0, 0, 0})
+                       double scale, cudaStream_t s)
 {
     const V *tw = (const V *)p->d_tw;
     const FourStep &f = p->four[a];
-    if (!f.on) return strided<V>(p->ax[a], in, out, tw, outer, W, backward, s, p->d_err, rm);
-    if (rm.in > 0) return cudaErrorInvalidValue;
+    if (!f.on) return strided<V>(p->ax[a], in, out, tw, outer, W, backward, s, p->d_err);
     V *tmp = (V *)p->d_four;
     cudaError_t e = strided<V>(p->ax[a], in, tmp, tw, outer, W * f.na, backward, s, p->d_err);
     if (e != cudaSuccess) return e;
     return fourstep<V>(f, tmp, out, tw, outer, W, backward, scale, s);
 }
 
-// Forward: N2 stage (c2c, or r2c into the padded workspace), N1 stage, N0 stage.
+// Forward: N2 stage (c2c, or r2c), N1 stage, N0 stage, all writing `out`.
 // With chunk_planes > 0 the N2 and N1 stages run slab by slab: N2 of slab c on
 // the caller's stream, N1 of slab c on the plan's second stream right after, so
 // the slab is still in L2 when N1 reads it; N2 of slab c+2 waits for N1 of slab c,
@@ -640,13 +621,11 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
-    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, nhp = p->nhp, B = p->batch;
+    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, B = p->batch;
     const long long P0 = B * n0;          // planes of all transforms of the batch
-    // padded R2C: N2 and N1 stages in the workspace, N0 stage converts to the compact `out`
-    V *o = (V *)out;
-    V *w = nhp != nh ? (V *)p->d_work : o;
+    V *w = (V *)out;                      // every forward stage writes `out` (the last ones in place)
     const long long plane_in = n1 * n2;   // elements of `in` per plane (reals for r2c)
-    const long long plane_w = n1 * nhp;   // complex elements of w per plane
+    const long long plane_w = n1 * nh;    // complex elements of `out` per plane
     auto zstage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
         if (p->kind == AFFT_C2C && p->four[2].on)
             return axis_stage<V>(p, 2, (const V *)in + p0 * plane_in, w + p0 * plane_w, np * n1, 1, 0, 1.0, st);
@@ -657,7 +636,7 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
     };
     auto ystage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
         if (n1 <= 1) return cudaSuccess;
-        return axis_stage<V>(p, 1, w + p0 * plane_w, w + p0 * plane_w, np, nhp, 0, 1.0, st);
+        return axis_stage<V>(p, 1, w + p0 * plane_w, w + p0 * plane_w, np, nh, 0, 1.0, st);
     };
     cudaError_t e = cudaSuccess;
     mark(p, 0, s);
@@ -686,15 +665,7 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
         if (ystage(0, P0, s) != cudaSuccess) return AFFT_ERR_CUDA;
         mark(p, 2, s);
     }
-    if (n0 > 1) {
-        const Remap rm = nhp != nh ? Remap{n1 * nh, (int)nhp, (int)nh} : Remap{0, 0, 0};
-        if (axis_stage<V>(p, 0, w, o, B, n1 * nhp, 0, 1.0, s, rm) != cudaSuccess) return AFFT_ERR_CUDA;
-    } else if (w != o) {
-        // one plane per transform: the compact output is the padded workspace without its pad column
-        if (cudaMemcpy2DAsync(o, nh * sizeof(V), w, nhp * sizeof(V), nh * sizeof(V), B * n1,
-                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return AFFT_ERR_CUDA;
-    }
+    if (n0 > 1 && axis_stage<V>(p, 0, w, w, B, n1 * nh, 0, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
     mark(p, 3, s);
     return AFFT_OK;
 }
@@ -706,15 +677,15 @@ int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
-    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, nhp = p->nhp, B = p->batch;
+    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, B = p->batch;
     const long long P0 = B * n0;
     const double scale = 1.0 / ((double)p->n[0] * (double)p->n[1] * (double)p->n[2]);
     // C2C works in `out`; c2r works in the plan's workspace and writes real `out` last.
     V *buf = p->kind == AFFT_C2C ? (V *)out : (V *)p->d_work;
-    const long long plane_w = n1 * nhp, plane_out = n1 * n2;
+    const long long plane_w = n1 * nh, plane_out = n1 * n2;
     auto ystage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
         if (n1 <= 1) return cudaSuccess;
-        return axis_stage<V>(p, 1, buf + p0 * plane_w, buf + p0 * plane_w, np, nhp, 1, 1.0, st);
+        return axis_stage<V>(p, 1, buf + p0 * plane_w, buf + p0 * plane_w, np, nh, 1, 1.0, st);
     };
     auto zstage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
         if (p->kind == AFFT_C2C && p->four[2].on)
@@ -725,15 +696,8 @@ int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
                          scale, st);
     };
     mark(p, 0, s);
-    const Remap rm = nhp != nh ? Remap{n1 * nhp, (int)nh, (int)nhp} : Remap{0, 0, 0};
-    if (n0 > 1 || nhp == nh) {
-        if (axis_stage<V>(p, 0, (const V *)in, buf, B, n1 * nh, 1, 1.0, s, rm) != cudaSuccess)
-            return AFFT_ERR_CUDA;
-    } else {
-        if (cudaMemcpy2DAsync(buf, nhp * sizeof(V), in, nh * sizeof(V), nh * sizeof(V), B * n1,
-                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return AFFT_ERR_CUDA;
-    }
+    // (n0 == 1: a copy of `in` into the buffer, which c2r then transforms without touching `in`)
+    if (axis_stage<V>(p, 0, (const V *)in, buf, B, n1 * nh, 1, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
     mark(p, 1, s);
     const int K = p->chunk_planes;
     if (K > 0) {
@@ -769,7 +733,7 @@ int configure_chunks(afft_plan *p, size_t bytes)
     p->chunk_bytes = bytes;
     p->chunk_planes = 0;
     const long long n0 = p->batch * p->n[0], n1 = p->n[1];
-    const size_t plane = (size_t)n1 * p->nhp * cplx_size(p->precision);
+    const size_t plane = (size_t)n1 * p->nh * cplx_size(p->precision);
     if (bytes == 0 || n1 <= 1 || n0 < 3 || plane == 0) return AFFT_OK;
     long long K = (long long)(bytes / plane);
     if (K < 1) K = 1;
@@ -797,16 +761,16 @@ int run_poisson(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
-    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, nhp = p->nhp, B = p->batch;
+    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, B = p->batch;
     const long long P0 = B * n0;
     const double scale = 1.0 / ((double)n0 * (double)n1 * (double)n2);
     V *w = (V *)p->d_work;
     mark(p, 0, s);
     if (r2c<V, T>(p->ax[2], (const T *)in, w, tw, tw + p->post_off, P0 * n1, s) != cudaSuccess) return AFFT_ERR_CUDA;
-    if (n1 > 1 && axis_stage<V>(p, 1, w, w, P0, nhp, 0, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n1 > 1 && axis_stage<V>(p, 1, w, w, P0, nh, 0, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
     mark(p, 1, s);
     const AxisPlan &x = p->ax[0];
-    const long long W = n1 * nhp;
+    const long long W = n1 * nh;
     if (n0 > 1 && x.pipe && !p->four[0].on && x.ks->poisson[0]) {
         alignas(64) CUtensorMap map;
         std::memset(&map, 0, sizeof map);
@@ -816,10 +780,10 @@ int run_poisson(afft_plan *p, const void *in, void *out, cudaStream_t s)
         long long tpo = (W + x.ks->pipe_lines - 1) / x.ks->pipe_lines, nt = B * tpo;
         const void *twdf = x.desc.twdf;
         unsigned *err = p->d_err;
-        int in1 = (int)n1, inhp = (int)nhp, inh = (int)nh;
+        int in1 = (int)n1, ipitch = (int)nh, inh = (int)nh;
         const V *win = w;
         void *args[] = {(void *)&win, (void *)&w, (void *)&map, (void *)&twa, (void *)&WW, (void *)&tpo, (void *)&nt,
-                        (void *)&err, (void *)&twdf, (void *)&in1, (void *)&inhp, (void *)&inh};
+                        (void *)&err, (void *)&twdf, (void *)&in1, (void *)&ipitch, (void *)&inh};
         const unsigned grid = (unsigned)std::min<long long>(nt, x.pipe_slots);
         if (cudaLaunchKernel(x.ks->poisson[tma ? 0 : 1], dim3(grid), dim3(x.ks->pipe_threads), args,
                              (size_t)x.ks->pipe_smem, s) != cudaSuccess)
@@ -828,15 +792,15 @@ int run_poisson(afft_plan *p, const void *in, void *out, cudaStream_t s)
         if (n0 > 1 && axis_stage<V>(p, 0, w, w, B, W, 0, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
         const KernelSet *g = p->precision == AFFT_F64 ? generic_kernels_f64() : generic_kernels_f32();
         long long planes = P0;
-        int a0 = (int)n0, a1 = (int)n1, a2 = (int)nhp, a3 = (int)nh;
+        int a0 = (int)n0, a1 = (int)n1, a2 = (int)nh, a3 = (int)nh;
         void *args[] = {(void *)&w, (void *)&planes, (void *)&a0, (void *)&a1, (void *)&a2, (void *)&a3};
-        const long long total = P0 * n1 * nhp;
+        const long long total = P0 * n1 * nh;
         const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 32);
         if (cudaLaunchKernel(g->poisson_mult, dim3(blocks), dim3(256), args, 0, s) != cudaSuccess) return AFFT_ERR_CUDA;
         if (n0 > 1 && axis_stage<V>(p, 0, w, w, B, W, 1, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
     }
     mark(p, 2, s);
-    if (n1 > 1 && axis_stage<V>(p, 1, w, w, P0, nhp, 1, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n1 > 1 && axis_stage<V>(p, 1, w, w, P0, nh, 1, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
     if (c2r<V, T>(p->ax[2], w, (T *)out, tw, tw + p->post_off, P0 * n1, scale, s) != cudaSuccess)
         return AFFT_ERR_CUDA;
     mark(p, 3, s);
@@ -1024,14 +988,14 @@ int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch,
         }
     }
     if (st == AFFT_OK && any_four) {
-        const size_t bytes = (size_t)batch * n[0] * n[1] * p->nhp * cplx_size(precision);
+        const size_t bytes = (size_t)batch * n[0] * n[1] * p->nh * cplx_size(precision);
         if (cudaMalloc(&p->d_four, bytes) != cudaSuccess) {
             p->d_four = nullptr;
             st = AFFT_ERR_NOMEM;
         }
     }
     if (st == AFFT_OK && kind == AFFT_R2C) {
-        p->work_bytes = (size_t)batch * n[0] * n[1] * p->nhp * cplx_size(precision);
+        p->work_bytes = (size_t)batch * n[0] * n[1] * p->nh * cplx_size(precision);
         if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) {
             p->d_work = nullptr;
             p->work_bytes = 0;
@@ -1246,11 +1210,10 @@ int afft_plan_tune(afft_plan *p, void *stream)
             if (p->precision == AFFT_F64) reshape_contig<double2>(p, best_t);
             else reshape_contig<float2>(p, best_t);
         }
-        // 2. pipelined or plain kernels for the strided stages (the padded r2c layout needs the
-        //    pipelined N0 stage for its column remap)
+        // 2. pipelined or plain kernels for the strided stages
         for (int a = 1; a >= 0; --a) {
             AxisPlan &ap = p->ax[a];
-            if (!ap.pipe_avail || (a == 0 && p->nhp != p->nh)) continue;
+            if (!ap.pipe_avail) continue;
             ap.pipe = true;
             const float with = measure();
             ap.pipe = false;
@@ -1258,7 +1221,7 @@ int afft_plan_tune(afft_plan *p, void *stream)
             ap.pipe = !(without > 0 && (with < 0 || without < with));
         }
         // 3. L2 slab schedule for arrays well beyond L2
-        const size_t array = (size_t)p->batch * p->n[0] * p->n[1] * p->nhp * c;
+        const size_t array = (size_t)p->batch * p->n[0] * p->n[1] * p->nh * c;
         if (array > ((size_t)192 << 20)) {
             size_t best_b = 0;
             configure_chunks(p, 0);
@@ -1295,7 +1258,7 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         buf, len,
         "{\"n\": [%lld, %lld, %lld], \"batch\": %lld, \"kind\": \"%s\", \"precision\": \"%s\", "
         "\"radix\": [\"%s\", \"%s\", \"%s\"], \"specialised\": [%d, %d, %d], \"four_step\": [%d, %d, %d], "
-        "\"pipelined\": [%d, %d], \"contig_lines\": %d, \"strided_lines\": [%d, %d], \"padded_row\": %lld, "
+        "\"pipelined\": [%d, %d], \"contig_lines\": %d, \"strided_lines\": [%d, %d], "
         "\"l2_slab_planes\": %d}",
         (long long)p->n[0], (long long)p->n[1], (long long)p->n[2], (long long)p->batch,
         p->kind == AFFT_C2C ? "c2c" : "r2c",
@@ -1303,7 +1266,7 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         !p->ax[0].ks->generic, !p->ax[1].ks->generic, !p->ax[2].ks->generic, p->four[0].on, p->four[1].on,
         p->four[2].on, p->ax[0].pipe, p->ax[1].pipe, p->ax[2].launch.lines,
         p->ax[0].pipe ? p->ax[0].ks->pipe_lines : p->ax[0].launch.lines,
-        p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, (long long)p->nhp, p->chunk_planes);
+        p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, p->chunk_planes);
     if (need < 0) return AFFT_ERR_CUDA;
     return (size_t)need < len ? AFFT_OK : AFFT_ERR_SIZE;
 }
@@ -1338,7 +1301,7 @@ int afft_plan_set_l2_chunk(afft_plan *p, size_t bytes)
 size_t afft_plan_l2_chunk(const afft_plan *p)
 {
     if (!p || p->chunk_planes <= 0) return 0;
-    return (size_t)p->chunk_planes * (size_t)p->n[1] * p->nhp * cplx_size(p->precision);
+    return (size_t)p->chunk_planes * (size_t)p->n[1] * p->nh * cplx_size(p->precision);
 }
 
 int afft_fill_uniform(void *dev_out, int64_t count, uint64_t seed, int precision, void *stream)

@@ -79,13 +79,10 @@ enum { KS_STRIDED_FWD = 0, KS_STRIDED_BWD, KS_CONTIG_FWD, KS_CONTIG_BWD, KS_R2C,
 // Pipelined strided kernels (persistent CTAs, double-buffered tiles), indexed
 // by PIPE_*.  Signature: (const V *in, V *out, CUtensorMap map, const V *tw,
 // long long W, long long tiles_per_outer, long long ntiles, unsigned *err,
-// long long Wout, int remap_in, int remap_out, const void *twdf, const unsigned
-// *mma) (twdf: the float-float twiddles of an FP64 plan, or null; mma: the
-// tensor-core DFT-16 table of a split-precision plan, or null); the TMA variants read through
-// `map`, the cp.async ones through `in`.  Input column c is stored to output
-// column c (remap_in == 0), or, with q = c / remap_in and k = c % remap_in,
-// to q * remap_out + k when k < remap_out and nowhere otherwise (used to move
-// between the compact and the padded half-spectrum layouts).
+// const void *twdf, const unsigned *mma) (twdf: the float-float twiddles of an
+// FP64 plan, or null; mma: the tensor-core DFT-16 table of a split-precision
+// plan, or null); the TMA variants read through `map`, the cp.async ones
+// through `in`.
 enum { PIPE_FWD_TMA = 0, PIPE_FWD_CPASYNC, PIPE_BWD_TMA, PIPE_BWD_CPASYNC, PIPE_COUNT };
 
 struct KernelSet {

@@ -97,11 +97,11 @@ template <typename V, typename CT = V> struct GlobalColsOut {
     }
 };
 
-// Output side of a strided tile whose columns are remapped between layouts:
-// every call comes from the thread that owns one column (line-fast maps with a
-// CTA size that is a multiple of the tile width), so the destination column
-// `col` (or -1 for "not stored") is resolved once per tile per thread.
-template <typename V, typename CT = V> struct GlobalColRemapOut {
+// Output side of a strided tile for passes whose every call comes from the
+// thread that owns one column (line-fast maps with a CTA size that is a
+// multiple of the tile width): the destination column `col` (or -1 for "not
+// stored") is resolved once per tile per thread.
+template <typename V, typename CT = V> struct GlobalColFixedOut {
     V *base;                       // &y[o][0][0]
     long long W;                   // output row pitch
     long long col;                 // this thread's output column, -1 to drop

@@ -234,30 +234,21 @@ __device__ __forceinline__ void pair_pass(const float2 *src, const float2 *__res
 }
 
 // Output of a tile's column l (tile columns start at c0), for passes whose
-// threads do not own fixed columns (the tensor-core radix-16 pass): column
-// c = c0 + l goes to c (remap_in == 0) or to q remap_out + k (c = q remap_in
-// + k, k < remap_out), and nowhere past the array's W columns.
+// threads do not own fixed columns (the tensor-core radix-16 pass).
 template <typename V> struct PipeColOut {
     V *base;                          // &y[o][0][0]
-    long long Wout, c0, W;
-    int remap_in, remap_out;
+    long long c0, W;
     __device__ __forceinline__ void operator()(int l, int p, V v) const
     {
-        long long c = c0 + l;
-        if (c >= W) return;
-        if (remap_in > 0) {
-            const long long q = c / remap_in, k = c - q * remap_in;
-            if (k >= remap_out) return;
-            c = q * remap_out + k;
-        }
-        base[(long long)p * Wout + c] = v;
+        const long long c = c0 + l;
+        if (c < W) base[(long long)p * W + c] = v;
     }
 };
 
 // The stage's global output for the pass kinds, resolved per thread per tile
 // (stored as V, computed as CT).
 template <typename V, typename CT = V> struct TileOut {
-    GlobalColRemapOut<V, CT> single;  // one column per thread
+    GlobalColFixedOut<V, CT> single;  // one column per thread
     PairGlobalOut pair;               // two columns per thread (float2 only)
     PipeColOut<V> cols;               // any column (split-precision radix-16 passes)
 };
@@ -322,8 +313,7 @@ template <class P, int S, typename V, bool TMA, bool Split = false>
 __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     k_strided_pipe(const V *__restrict__ in, V *out, const __grid_constant__ CUtensorMap tmap,
                    const V *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
-                   unsigned *err, long long Wout, int remap_in, int remap_out, const void *twdf,
-                   const unsigned *mma)
+                   unsigned *err, const void *twdf, const unsigned *mma)
 {
     using Sh = PipeShape<P, V>;
     constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
@@ -369,12 +359,7 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
             cp_async_commit();
         }
     };
-    auto out_col = [&](long long c) -> long long {
-        if (c >= W) return -1;
-        if (remap_in <= 0) return c;
-        const long long q = c / remap_in, k = c - q * remap_in;
-        return k < remap_out ? q * remap_out + k : -1;
-    };
+    auto out_col = [&](long long c) -> long long { return c < W ? c : -1; };
 
     issue(t, 0);
     for (int i = 0;; ++i) {
@@ -396,21 +381,21 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
         const long long o = t / tiles_per_outer;
         const long long c0 = (t - o * tiles_per_outer) * LINES;
         TileOut<V> to;
-        to.single = GlobalColRemapOut<V>{out + o * (long long)N * Wout, Wout, out_col(c0 + (tid & (LINES - 1)))};
-        to.cols = PipeColOut<V>{out + o * (long long)N * Wout, Wout, c0, W, remap_in, remap_out};
+        to.single = GlobalColFixedOut<V>{out + o * (long long)N * W, W, out_col(c0 + (tid & (LINES - 1)))};
+        to.cols = PipeColOut<V>{out + o * (long long)N * W, c0, W};
         if constexpr (sizeof(V) == 8) {
             const int lp = tid % (LINES / 2 > 0 ? LINES / 2 : 1);
             const long long a = out_col(c0 + 2 * lp), bcol = out_col(c0 + 2 * lp + 1);
-            float2 *base = reinterpret_cast<float2 *>(out + o * (long long)N * Wout);
-            const bool vec = a >= 0 && bcol == a + 1 && (a % 2) == 0 && (Wout % 2) == 0 &&
+            float2 *base = reinterpret_cast<float2 *>(out + o * (long long)N * W);
+            const bool vec = a >= 0 && bcol == a + 1 && (a % 2) == 0 && (W % 2) == 0 &&
                              (reinterpret_cast<unsigned long long>(base) & 15) == 0;
-            to.pair = PairGlobalOut{base, Wout, a, bcol, vec};
+            to.pair = PairGlobalOut{base, W, a, bcol, vec};
         }
         bool done = false;
         if constexpr (std::is_same<V, double2>::value && P::npass >= 2) {
             if (twdf) {
                 TileOut<V, dcx> tdf;
-                tdf.single = GlobalColRemapOut<V, dcx>{to.single.base, to.single.W, to.single.col};
+                tdf.single = GlobalColFixedOut<V, dcx>{to.single.base, to.single.W, to.single.col};
                 done = pipe_df<Sh, S, N>(typename P::seq{}, buf0 + b * TILE, scratch, (const dcx *)twdf, tdf);
             }
         }
@@ -487,7 +472,7 @@ struct PairGlobalOutOdd {
     }
 };
 struct TileOutOdd {
-    GlobalColRemapOut<float2> single;
+    GlobalColFixedOut<float2> single;
     PairGlobalOutOdd pair;
 };
 
@@ -520,12 +505,12 @@ __device__ __forceinline__ void rp_passes(Seq<R0, Rest...>, float2 *X, float2 *C
 
 // Persistent, double-buffered strided stage over odd-width complex64 rows (same
 // argument list as k_strided_pipe; the tensor map views [outer][n/2][2W] with
-// boxes of 18 x n/2; no column remap).
+// boxes of 18 x n/2).
 template <class P, int S>
 __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
     k_strided_pipe_rp(const float2 *__restrict__, float2 *out, const __grid_constant__ CUtensorMap tmap,
                       const float2 *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
-                      unsigned *err, long long, int, int, const void *, const unsigned *)
+                      unsigned *err, const void *, const unsigned *)
 {
     using V = float2;
     using Sh = PipeShape<P, V>;
@@ -575,7 +560,7 @@ __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
         V *obase = out + o * (long long)N * W;
         const long long a = c0 + 2 * lp;
         TileOutOdd to;
-        to.single = GlobalColRemapOut<V>{obase, W, c0 + l < W ? c0 + l : -1};
+        to.single = GlobalColFixedOut<V>{obase, W, c0 + l < W ? c0 + l : -1};
         to.pair = PairGlobalOutOdd{obase, W, a < W ? a : -1, a + 1 < W ? a + 1 : -1,
                                    a + 1 < W && (reinterpret_cast<unsigned long long>(obase) & 15) == 0};
         rp_passes<Sh, S, N>(typename P::seq{}, buf0 + b * TILE_RP, scratch, tw, to, l);
@@ -718,7 +703,7 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
                 for (int e = tid; e < TILE; e += NT) Y[e] = Conv<dcx, double2>::in(X[e], &f);
                 if (df_tile_ok(f)) {
                     TileOut<V, dcx> g;
-                    g.single = GlobalColRemapOut<V, dcx>{obase, W, c < W ? c : -1};
+                    g.single = GlobalColFixedOut<V, dcx>{obase, W, c < W ? c : -1};
                     poisson_tile<Sh, N>(Y, reinterpret_cast<dcx *>(X), (const dcx *)twdf, g, n1, k1, k2, keep);
                     done = true;
                 }
@@ -726,7 +711,7 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
         }
         if (!done) {
             TileOut<V> g;
-            g.single = GlobalColRemapOut<V>{obase, W, c < W ? c : -1};
+            g.single = GlobalColFixedOut<V>{obase, W, c < W ? c : -1};
             if constexpr (sizeof(V) == 8) {
                 const int lp = tid % (LINES / 2 > 0 ? LINES / 2 : 1);
                 const long long a = c0 + 2 * lp;
