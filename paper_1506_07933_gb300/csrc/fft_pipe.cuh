@@ -751,7 +751,7 @@ template <class F, typename V> KernelSet kernel_set(int n, int npass, const int 
     if constexpr (!F::generic) {
         // n = 1024 would need 64-byte tile rows to double-buffer; measured slower than the
         // single-buffered kernel with the same rows, so it keeps the non-pipelined kernel.
-        if constexpr (F::plan::npass > 0 && F::plan::n < 1024) {
+        if constexpr (F::plan::npass > 0 && F::plan::n <= 1024) {
             using P = typename F::plan;
             using Sh = PipeShape<P, V>;
             k.pipe[PIPE_FWD_TMA] = (const void *)k_strided_pipe<P, -1, V, true, F::split>;

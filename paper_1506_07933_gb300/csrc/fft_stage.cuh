@@ -295,7 +295,7 @@ struct Generic {
     static constexpr bool split = false;
     using plan = LinePlan<0>;
     template <typename V> static constexpr int threads() { return 256; }
-    static constexpr int min_blocks = 1;
+    static constexpr int min_blocks = 2;
 };
 // Generic complex64 kernels of split-precision plans: radix-16 passes on the
 // tensor cores, otherwise as Generic.
