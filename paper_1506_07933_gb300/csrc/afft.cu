@@ -323,9 +323,10 @@ int plan_shapes(afft_plan *p)
     const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh, B = p->batch;
     // strided stages (and the first half of a four-step contiguous axis): persistent
     // double-buffered kernels where the family has them.  A 1024-point tile has 64-byte rows
-    // (two buffers must fit); with rows megabytes apart (the N0 stage of a 1024^3 array) the
-    // non-pipelined kernel's many CTAs measured faster (6.84 vs 5.48 ms), with rows a few KB
-    // apart the pipelined one (3.04 vs 3.77 ms).
+    // (two buffers must fit).  Measured on 1024-point N0/N1 stages: rows 8 KB apart 3.04 ms
+    // against 3.77 ms for the non-pipelined kernel (1024^3), 2 MB apart 1.20 against 1.35 ms
+    // (1024 x 512^2), 8 MB apart 6.83 against 5.48 ms (1024^3): beyond 4 MB the many CTAs of
+    // the non-pipelined kernel win.
     const long long row_bytes[3] = {n1 * nh * (long long)elem, nh * (long long)elem, (long long)elem};
     for (int a = 0; a < 3; ++a) {
         if (a == 2 && !p->four[2].on) continue;
@@ -333,7 +334,7 @@ int plan_shapes(afft_plan *p)
         ap.pipe = false;
         const KernelSet *ks = ap.ks;
         if (ks->generic || !ks->pipe[PIPE_FWD_TMA] || ks->pipe_smem > max_smem) continue;
-        if (ks->n >= 1024 && row_bytes[a] > (1LL << 20)) continue;
+        if (ks->n >= 1024 && row_bytes[a] > (1LL << 22)) continue;
         for (int k = 0; k < PIPE_COUNT; ++k)
             if (cudaFuncSetAttribute(ks->pipe[k], cudaFuncAttributeMaxDynamicSharedMemorySize, ks->pipe_smem) !=
                 cudaSuccess)
