@@ -168,6 +168,17 @@ int afft_plan_destroy(afft_plan *p);
  */
 int afft_plan_device_status(afft_plan *p);
 
+/*
+ * Failure-detection self-test: launches on `cuda_stream` one CTA whose bounded
+ * wait cannot be satisfied (an mbarrier that nothing arrives at), for at most
+ * limit_us microseconds (1 ... 2,000,000); it then records the timeout in the
+ * plan's flag exactly as the pipelined kernels do and exits, so the next
+ * afft_plan_device_status returns AFFT_ERR_TIMEOUT (once).  No memory is
+ * touched besides the flag and no fault is raised: the device stays usable.
+ * AFFT_ERR_SIZE for limit_us out of range.  Asynchronous.
+ */
+int afft_plan_wait_probe(afft_plan *p, int limit_us, void *cuda_stream);
+
 /* Bytes of device workspace the plan holds (0 for a NULL plan). */
 size_t afft_plan_workspace_bytes(const afft_plan *p);
 

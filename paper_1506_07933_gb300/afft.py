@@ -41,7 +41,7 @@ EXPORTS = [
     "afft_plan_timing_begin", "afft_plan_timing_end", "afft_c2r_noalloc",
     "afft_plan_device_status", "afft_plan_set_l2_chunk", "afft_plan_l2_chunk",
     "afft_plan_create_batched", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
-    "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson",
+    "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe",
 ]
 
 _lib = None
@@ -87,6 +87,7 @@ def load(path: str = None):
     lib.afft_plan_timing_end.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(c_int)]
     lib.afft_c2r_noalloc.argtypes = [i64p, c_int, vp, vp, vp]
     lib.afft_plan_device_status.argtypes = [vp]
+    lib.afft_plan_wait_probe.argtypes = [vp, c_int, vp]
     lib.afft_plan_set_l2_chunk.argtypes = [vp, sz]
     lib.afft_plan_l2_chunk.argtypes = [vp]
     lib.afft_plan_l2_chunk.restype = sz
@@ -95,7 +96,7 @@ def load(path: str = None):
               "afft_plan_launches", "afft_fill_uniform", "afft_plan_timing_begin",
               "afft_plan_timing_end", "afft_c2r_noalloc", "afft_plan_device_status",
               "afft_plan_set_l2_chunk", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
-              "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson"):
+              "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -300,6 +301,11 @@ class Plan:
     def device_status(self) -> int:
         """Synchronises; returns 0, or 11 (AFFT_ERR_TIMEOUT) if a bounded wait ran out since the last call."""
         return int(load().afft_plan_device_status(self._p))
+
+    def wait_probe(self, limit_us: int, stream=None) -> None:
+        """Failure-detection self-test: a kernel whose bounded wait can only run out records a
+        timeout in this plan's flag (see afft_plan_wait_probe); device_status() then reports it."""
+        _check(load().afft_plan_wait_probe(self._p, int(limit_us), _stream_handle(stream)), "afft_plan_wait_probe")
 
     def timing_begin(self, capacity: int) -> None:
         """Record per-stage CUDA events for the next ``capacity`` executions."""

@@ -15,10 +15,18 @@
 
 #include <cuda.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/afft.h"
 #include "afft_internal.h"
 
 using namespace afft;
+
+// An NVTX range around a host call (visible in Nsight timelines; inert without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct AxisPlan {
     StageDesc desc;
@@ -1022,6 +1030,7 @@ int afft_execute_forward(afft_plan *p, const void *in, void *out, void *stream)
     const int st = check_exec(p, in, out, 0);
     if (st != AFFT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    const NvtxRange range("afft_execute_forward");
     return p->precision == AFFT_F64 ? run_forward<double2>(p, in, out, s) : run_forward<float2>(p, in, out, s);
 }
 
@@ -1030,6 +1039,7 @@ int afft_execute_backward(afft_plan *p, const void *in, void *out, void *stream)
     const int st = check_exec(p, in, out, 1);
     if (st != AFFT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    const NvtxRange range("afft_execute_backward");
     return p->precision == AFFT_F64 ? run_backward<double2>(p, in, out, s)
                                     : run_backward<float2>(p, in, out, s);
 }
@@ -1042,6 +1052,7 @@ int afft_execute_poisson(afft_plan *p, const void *in, void *out, void *stream)
     const size_t nb = in_bytes(p);
     if (overlaps(in, nb, out, nb)) return AFFT_ERR_INPLACE;
     cudaStream_t s = (cudaStream_t)stream;
+    const NvtxRange range("afft_execute_poisson");
     return p->precision == AFFT_F64 ? run_poisson<double2>(p, in, out, s) : run_poisson<float2>(p, in, out, s);
 }
 
@@ -1135,6 +1146,16 @@ int afft_plan_timing_end(afft_plan *p, float *ms, int *count)
     p->timing_cap = 0;  // stop recording; the events are kept for the next begin
     p->timing_count = 0;
     return st;
+}
+
+int afft_plan_wait_probe(afft_plan *p, int limit_us, void *stream)
+{
+    if (!p) return AFFT_ERR_NULL;
+    if (limit_us < 1 || limit_us > 2000000) return AFFT_ERR_SIZE;
+    if (!p->d_err) return AFFT_ERR_CUDA;
+    return launch_wait_probe(p->d_err, (unsigned long long)limit_us * 1000ull, (cudaStream_t)stream) == cudaSuccess
+               ? AFFT_OK
+               : AFFT_ERR_CUDA;
 }
 
 int afft_plan_device_status(afft_plan *p)

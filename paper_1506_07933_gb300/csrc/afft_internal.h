@@ -123,6 +123,9 @@ const KernelSet *generic_kernels_f64();
 // Generic complex64 kernels whose radix-16 passes run on the tensor cores
 // (split-precision plans), and the device table of their DFT-16 fragments
 // (kSplitTableBytes, written by split_fragments on `stream`).
+// Failure-detection self-test (selftest.cu): one CTA waits at most limit_ns on
+// an mbarrier that nothing completes, then sets *err.
+cudaError_t launch_wait_probe(unsigned *err, unsigned long long limit_ns, cudaStream_t stream);
 const KernelSet *generic_kernels_split();
 const KernelSet *spec_kernels_split(int n);
 constexpr size_t kSplitTableBytes = 2 * 32 * 32 * sizeof(unsigned);

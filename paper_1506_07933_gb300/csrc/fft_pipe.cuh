@@ -63,14 +63,15 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Waits for the given phase of the barrier for at most ~2 s.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
+// Waits for the given phase of the barrier for at most limit_ns (default ~2 s).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
+                                                  unsigned long long limit_ns = 2000000000ull)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0 && global_ns() - t0 > 2000000000ull) return false;
+        if ((it & 255u) == 0 && global_ns() - t0 > limit_ns) return false;
     }
 }
 

@@ -41,6 +41,7 @@ import torch
 from . import afft, synth
 
 DT = {"f32": torch.float32, "f64": torch.float64}
+_ALLOC_ERRORS = (MemoryError, RuntimeError)   # torch's OutOfMemoryError and afft.AfftError are RuntimeErrors
 BYTES = {"f32": 4, "f64": 8}
 SIZES = (64, 128, 192, 256, 384, 512)
 
@@ -176,6 +177,7 @@ class PoissonServer:
         self.plans = {}           # (n, prec, B) -> [idle (plan, f, u)]
         self.held = 0             # bytes of plans and buffers the server holds
         self.results = {}
+        self.alloc_failures = 0   # plan or buffer allocations the device refused
 
     def _order(self, queue):
         """Waiting (n, precision) queues in admission order: oldest head first ("fifo"), or
@@ -204,16 +206,17 @@ class PoissonServer:
     def _evict(self, need, keep):
         """Free idle plans and buffers of other keys (largest first) until `need` more bytes fit."""
         idle = sorted((k for k, ps in self.plans.items() if ps and k != keep), key=lambda k: -self._footprint(*k))
+        freed = False
         for k in idle:
             while self.plans[k] and self.held + need > self.budget:
                 self.plans[k].pop()[0].close()
                 self.held -= self._footprint(*k)
+                freed = True
             if self.held + need <= self.budget:
                 break
-        if self.held + need <= self.budget:
+        if freed:
             torch.cuda.empty_cache()
-            return True
-        return False
+        return self.held + need <= self.budget
 
     def _take(self, n, prec, B):
         key = (n, prec, B)
@@ -224,13 +227,30 @@ class PoissonServer:
                 raise MemoryError("a %d^3 %s batch of %d does not fit the HBM budget" % (n, prec, B))
             if self.held + need > self.budget and not self._evict(need, key):
                 return None
-            p = afft.Plan((n, n, n), "r2c", prec, batch=B if B > 1 else None)
-            shape = (B, n, n, n) if B > 1 else (n, n, n)
-            f = torch.empty(shape, dtype=DT[prec], device="cuda") if B > 1 else None
-            u = torch.empty(shape, dtype=DT[prec], device="cuda")
+            try:
+                entry = self.alloc(n, prec, B)
+            except _ALLOC_ERRORS:
+                # the device is fuller than the budget assumed (another user, fragmentation):
+                # free every idle plan of other sizes and try once more, else wait
+                self._evict(self.budget + 1, key)
+                try:
+                    entry = self.alloc(n, prec, B)
+                except _ALLOC_ERRORS:
+                    self.alloc_failures += 1
+                    return None
             self.held += need
-            idle.append((p, f, u))
+            idle.append(entry)
         return idle.pop()
+
+    @staticmethod
+    def alloc(n, prec, B):
+        """A batched plan and its buffers (f only for B > 1; u).  Replaceable, e.g. by tests that
+        inject allocation failures."""
+        p = afft.Plan((n, n, n), "r2c", prec, batch=B if B > 1 else None)
+        shape = (B, n, n, n) if B > 1 else (n, n, n)
+        f = torch.empty(shape, dtype=DT[prec], device="cuda") if B > 1 else None
+        u = torch.empty(shape, dtype=DT[prec], device="cuda")
+        return p, f, u
 
     def _give(self, key, entry):
         self.plans[key].append(entry)
@@ -325,6 +345,9 @@ class PoissonServer:
                 ev = torch.cuda.Event()
                 ev.record(self.slots[si])
                 busy[si] = (ev, group, entry, (n, prec, B))
+            if not busy and any(queue.values()):
+                # nothing runs and nothing could be admitted: no memory will free up
+                raise MemoryError("cannot admit any waiting request: the device refused every allocation")
             if not busy and not any(queue.values()) and pending:
                 time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.0005)))
         wall = time.perf_counter() - t0

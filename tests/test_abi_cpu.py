@@ -76,6 +76,7 @@ def test_null_arguments(lib):
     assert lib.afft_plan_workspace_bytes(None) == 0
     assert lib.afft_plan_input_bytes(None) == 0
     assert lib.afft_plan_launches(None, 0) == 0
+    assert lib.afft_plan_wait_probe(None, 1000, None) == 1
 
 
 def test_status_strings(lib):

@@ -357,6 +357,26 @@ def test_fill_uniform_matches_cpu_definition():
     assert np.array_equal(t.cpu().numpy(), ref)
 
 
+def test_bounded_wait_reports_a_timeout_and_the_device_stays_usable():
+    """Failure detection without a fault: a wait that nothing can satisfy runs out after its
+    limit, the plan's status reports AFFT_ERR_TIMEOUT once, and transforms keep working."""
+    shape = (16, 24, 32)
+    x = synth.uniform_complex(shape, 77).astype(np.complex64)
+    with afft.Plan(shape, "c2c", "f32") as p:
+        assert p.device_status() == 0
+        p.wait_probe(2000)
+        torch.cuda.synchronize()
+        assert p.device_status() == 11
+        assert p.device_status() == 0          # reported once, then cleared
+        y = p.forward(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        assert p.device_status() == 0
+    report("c2c after a probed timeout", oracle.rel_l2(y.cpu().numpy(), oracle.c2c(x, -1, "fft")), TOL["f32"])
+    with pytest.raises(afft.AfftError):
+        with afft.Plan(shape, "c2c", "f32") as p:
+            p.wait_probe(0)
+
+
 def test_plans_are_independent():
     a = afft.Plan((8, 12, 16), "c2c", "f32")
     b = afft.Plan((8, 12, 16), "r2c", "f64")

@@ -1,6 +1,8 @@
 """Host-side logic of the Poisson request loop (no GPU)."""
 import math
 
+import pytest
+
 import numpy as np
 
 from paper_1506_07933_gb300 import serve
@@ -52,3 +54,38 @@ def test_batch_cap_follows_the_byte_budget():
     assert s._batch(128, "f32", 100) == 8 and s._batch(512, "f64", 5) == 1
     # a single request is solved from its own buffer: no gathered input in its footprint
     assert s._footprint(64, "f32", 2) - 2 * s._footprint(64, "f32", 1) == 2 * 64 ** 3 * 4
+
+
+def test_admission_survives_injected_allocation_failures():
+    """Admission without a GPU: an allocation the device refuses (injected) evicts the idle plans
+    of other sizes and retries once; a second refusal leaves the request waiting (None) and is
+    counted.  The budget itself still refuses a batch that can never fit."""
+    closed = []
+
+    class FakePlan:
+        def close(self):
+            closed.append(self)
+
+    srv = serve.PoissonServer.__new__(serve.PoissonServer)
+    srv.budget, srv.max_batch_bytes, srv.max_batch = 1 << 40, 64 << 20, 16
+    srv.plans, srv.held, srv.alloc_failures = {}, 0, 0
+    refusals = {"left": 1}
+
+    def alloc(n, prec, B):
+        if refusals["left"] > 0:
+            refusals["left"] -= 1
+            raise MemoryError("injected allocation failure")
+        return FakePlan(), None, object()
+
+    srv.alloc = alloc
+    srv.plans[(64, "f32", 1)] = [(FakePlan(), None, object())]
+    srv.held = srv._footprint(64, "f32", 1)
+    entry = srv._take(128, "f32", 1)
+    assert entry is not None and len(closed) == 1 and srv.plans[(64, "f32", 1)] == []
+    assert srv.held == srv._footprint(128, "f32", 1)
+    refusals["left"] = 2
+    assert srv._take(256, "f32", 1) is None and srv.alloc_failures == 1
+    assert srv.held == srv._footprint(128, "f32", 1)
+    srv.budget = 1 << 20
+    with pytest.raises(MemoryError):
+        srv._take(512, "f64", 1)
