@@ -548,17 +548,19 @@ __global__ void k_poisson_mult(V *x, long long planes, int n0, int n1, int nhp, 
 // then the radices in pass order).  Split-precision plans use the sequences of
 // AFFT_SPLIT_LINE_PLANS (as many radix-16 passes as the length allows), and
 // the FP32 kernels for the other lengths of AFFT_LINE_PLANS (no radix-16 pass).
-// (Groups A-D only split the complex128 instantiations over translation units
+// (Groups A-E only split the complex128 instantiations over translation units
 // that compile in parallel.)
 #define AFFT_LINE_PLANS_A(X)                                                                        \
     X(1) X(2, 2) X(4, 4) X(8, 8) X(16, 16) X(24, 8, 3) X(32, 8, 4) X(48, 16, 3) X(60, 4, 3, 5) X(64, 8, 8)
 #define AFFT_LINE_PLANS_B(X) X(80, 16, 5) X(96, 8, 4, 3) X(120, 8, 3, 5) X(128, 16, 8) X(160, 8, 4, 5) X(192, 8, 8, 3)
 #define AFFT_LINE_PLANS_C(X) X(256, 16, 16) X(384, 16, 8, 3)
 #define AFFT_LINE_PLANS_D(X) X(512, 8, 8, 8) X(1024, 16, 8, 8)
-#define AFFT_LINE_PLANS(X) AFFT_LINE_PLANS_A(X) AFFT_LINE_PLANS_B(X) AFFT_LINE_PLANS_C(X) AFFT_LINE_PLANS_D(X)
+#define AFFT_LINE_PLANS_E(X) X(2048, 16, 16, 8) X(4096, 16, 16, 16)
+#define AFFT_LINE_PLANS(X)                                                                          \
+    AFFT_LINE_PLANS_A(X) AFFT_LINE_PLANS_B(X) AFFT_LINE_PLANS_C(X) AFFT_LINE_PLANS_D(X) AFFT_LINE_PLANS_E(X)
 #define AFFT_SPLIT_LINE_PLANS(X)                                                                    \
     X(16, 16) X(32, 16, 2) X(48, 16, 3) X(64, 16, 4) X(80, 16, 5) X(96, 16, 3, 2) X(128, 16, 8)     \
     X(160, 16, 5, 2) X(192, 16, 4, 3) X(256, 16, 16) X(384, 16, 8, 3) X(512, 16, 16, 2)             \
-    X(1024, 16, 16, 4)
+    X(1024, 16, 16, 4) X(2048, 16, 16, 8) X(4096, 16, 16, 16)
 
 }  // namespace afft

@@ -1,5 +1,5 @@
-// kernels_f64.cu -- the double2 kernel families: the specialised ones (four
-// translation units, kernels_f64_[a-d].cu) and the generic family.
+// kernels_f64.cu -- the double2 kernel families: the specialised ones (five
+// translation units, kernels_f64_[a-e].cu) and the generic family.
 #include "kernel_tables.cuh"
 
 namespace afft {
@@ -8,10 +8,12 @@ const KernelSet *spec_kernels_f64_a(int n);
 const KernelSet *spec_kernels_f64_b(int n);
 const KernelSet *spec_kernels_f64_c(int n);
 const KernelSet *spec_kernels_f64_d(int n);
+const KernelSet *spec_kernels_f64_e(int n);
 
 const KernelSet *spec_kernels_f64(int n)
 {
-    for (auto *f : {spec_kernels_f64_a, spec_kernels_f64_b, spec_kernels_f64_c, spec_kernels_f64_d})
+    for (auto *f : {spec_kernels_f64_a, spec_kernels_f64_b, spec_kernels_f64_c, spec_kernels_f64_d,
+                    spec_kernels_f64_e})
         if (const KernelSet *k = f(n)) return k;
     return nullptr;
 }

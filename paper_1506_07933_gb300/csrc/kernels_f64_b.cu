@@ -1,6 +1,6 @@
 // kernels_f64_b.cu -- the double2 specialised families of the line lengths in
 // AFFT_LINE_PLANS_B (the complex128 instantiations are the slowest to compile,
-// so they are split over four translation units).
+// so they are split over five translation units).
 #include "kernel_tables.cuh"
 
 namespace afft {
