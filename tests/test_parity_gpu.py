@@ -289,6 +289,30 @@ def test_c2c_1024cubed_full_size_properties():
         report("c2c 1024^3 f32 plane-wave leakage", rest / N, TOL["f32"])
 
 
+def test_c2c_1024_point_rows_megabytes_apart_separable_input():
+    """An N0 stage of 1024-point lines whose rows lie more than 1 MB apart, checked over the
+    whole array: a separable input a[j0] b[j1] c[j2] has the separable spectrum A[k0] B[k1] C[k2]
+    (the oracle's 1-D DFTs); both directions."""
+    n0, n1, n2 = 1024, 384, 384
+    a = synth.uniform_complex((n0, 1, 1), 901)
+    b = synth.uniform_complex((1, n1, 1), 902)
+    c = synth.uniform_complex((1, 1, n2), 903)
+    A, B, C = (oracle.c2c(v, -1, "fft") for v in (a, b, c))
+    dev = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    x = (dev(a) * dev(b) * dev(c)).to(torch.complex64)
+    with afft.Plan((n0, n1, n2), "c2c", "f32") as p:
+        X = p.forward(x)
+        y = p.backward(X)
+        torch.cuda.synchronize()
+    ref = dev(A) * dev(B) * dev(C)
+    err = float(torch.linalg.vector_norm(X.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref))
+    del ref
+    report("c2c 1024x384x384 separable", err, TOL["f32"])
+    x64 = x.to(torch.complex128)
+    rt = float(torch.linalg.vector_norm(y.to(torch.complex128) - x64) / torch.linalg.vector_norm(x64))
+    report("c2c 1024x384x384 round trip", rt, TOL["f32"])
+
+
 # --- the boundary's behaviour on a GPU ------------------------------------------------
 
 def test_in_place_and_overlap_are_rejected():
