@@ -150,7 +150,7 @@ template <typename V, typename CT = V> struct C2RPre {
     const V *base;                 // &X[b0][0]
     const CT *post_tw;             // w_{2M}^k forward, k = 0..M
     int M;
-    int ld;                        // line stride (M + 1 compact, more when padded)
+    int ld;                        // line stride (M + 1 for the compact layout)
     int valid;
     DfFlags *bad;
     __device__ __forceinline__ CT operator()(int l, int k) const

@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     const GlobalLines<V> src{reinterpret_cast<const V *>(in) + b0 * M, M, valid};
     const SmemLines<V> tile{sm, M};
     const MapButterflyFast map{};
-    const int ld = d.ld > 0 ? d.ld : M + 1;  // output line stride (padded layouts leave a gap)
+    const int ld = d.ld > 0 ? d.ld : M + 1;  // output line stride (d.ld > 0: lines further apart)
     V *o = out + b0 * ld;
     if constexpr (UseDf<F, V>::value) {
         if (d.twdf) {
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(256, 1)
     run_generic<S, true, false, Split>(d, tw, sm, lines, log2_lines, MapLineFast{log2_lines}, src, dst);
 }
 
-// Spectral Poisson multiply on a half spectrum [planes][n1][nhp] (planes =
+// Spectral Poisson multiply on a half spectrum [planes][n1][nhp] (rows of nhp >= nh elements; planes =
 // batch * n0): bin (k0, k1, k2) times 1/|k|^2 with wrapped integer wavenumbers,
 // k = 0 and pad columns (k2 >= nh) set to zero.  Used when the N0 stage of a
 // plan cannot run the fused pipelined operator.

@@ -161,7 +161,8 @@ class PoissonServer:
     """Continuous-batching Poisson server (see the module docstring)."""
 
     def __init__(self, pool: RhsPool, slots: int = 4, hbm_budget: int = None, max_batch_bytes: int = 64 << 20,
-                 max_batch: int = 16, policy: str = "sjf", large_bytes: int = 256 << 20):
+                 max_batch: int = 16, policy: str = "sjf", large_bytes: int = 256 << 20,
+                 age_ms: float = 8.0):
         self.pool = pool
         # slots [0, slots/2) are high-priority streams for small groups; the rest take large ones
         lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
@@ -170,6 +171,7 @@ class PoissonServer:
                      [torch.cuda.Stream(priority=lo) for _ in range(slots - self.n_fast)]
         self.policy = policy
         self.large_bytes = large_bytes
+        self.age = age_ms * 1e-3   # a head request older than this is admitted first ("sjf")
         free, _ = torch.cuda.mem_get_info()
         self.budget = hbm_budget if hbm_budget is not None else int(free * 0.6)
         self.max_batch_bytes = max_batch_bytes
@@ -179,13 +181,17 @@ class PoissonServer:
         self.results = {}
         self.alloc_failures = 0   # plan or buffer allocations the device refused
 
-    def _order(self, queue):
+    def _order(self, queue, now=None):
         """Waiting (n, precision) queues in admission order: oldest head first ("fifo"), or
-        smallest group work first, ties by age ("sjf")."""
+        smallest group work first, ties by age ("sjf"), except that queues whose head has waited
+        longer than `age_ms` go first, oldest first (so large solves are not starved)."""
         keys = [k for k, q in queue.items() if q]
         if self.policy == "fifo":
             return sorted(keys, key=lambda k: queue[k][0].arrival)
-        return sorted(keys, key=lambda k: (k[0] ** 3 * BYTES[k[1]], queue[k][0].arrival))
+        late = sorted((k for k in keys if now is not None and now - queue[k][0].arrival > self.age),
+                      key=lambda k: queue[k][0].arrival)
+        rest = sorted((k for k in keys if k not in late), key=lambda k: (k[0] ** 3 * BYTES[k[1]], queue[k][0].arrival))
+        return late + rest
 
     def _cap(self, n, prec):
         one = n ** 3 * BYTES[prec]
@@ -321,15 +327,17 @@ class PoissonServer:
                     done.append((group, key))
                     del busy[si]
             free_slots = [i for i in range(len(self.slots)) if i not in busy]
-            for (n, prec) in self._order(queue):
+            now = time.perf_counter() - t0
+            for (n, prec) in self._order(queue, now):
                 if not free_slots:
                     break
                 q = queue[(n, prec)]
                 B = self._batch(n, prec, len(q))
                 large = B * n ** 3 * BYTES[prec] >= self.large_bytes
-                # large groups run on the normal-priority slots only; small ones prefer the
-                # high-priority slots, so their kernels are dispatched ahead of a large one's
-                usable = [i for i in free_slots if i >= self.n_fast] if large else free_slots
+                overdue = now - q[0].arrival > self.age
+                # large groups run on the normal-priority slots; small ones, and any group whose
+                # head is overdue, prefer the high-priority slots, whose kernels are dispatched first
+                usable = [i for i in free_slots if i >= self.n_fast] if (large and not overdue) else free_slots
                 if not usable:
                     continue
                 entry = self._take(n, prec, B)
