@@ -153,6 +153,9 @@ template <class P, typename V> struct PipeShape {
     }
     static constexpr int threads = threads_for(typename P::seq{});
     static_assert(threads % lines == 0, "each thread must own fixed columns of the tile");
+    // butterflies (or pairs) per thread that cover a radix-r pass with `threads` threads: in-place
+    // passes hold all of them in registers across the barrier, so no more than needed
+    __host__ __device__ static constexpr int covering(int r) { return (units(r) + threads - 1) / threads; }
     using seq = typename P::seq;
     static constexpr int npass = P::npass;
     static constexpr int tile = P::n * lines;                       // complex elements per tile
@@ -195,25 +198,26 @@ struct PairGlobalOut {
     }
 };
 
-// One radix-R Stockham pass over a [N][2^LG] float2 tile, out of place; the
-// thread's butterflies are (column pair lp, butterfly j), reading both
-// columns' R values with 16-byte loads and sharing the twiddles.
-template <int R, int S, int N, int Ns, int LG, int NT, int B, class Dst>
+// One radix-R Stockham pass over a [N][2^LG] float2 tile; the thread's
+// butterflies are (column pair lp, butterfly j), reading both columns' R
+// values with 16-byte loads and sharing the twiddles.  InPlace: every read of
+// the CTA precedes a barrier, every write follows it (src and dst may alias).
+template <int R, int S, int N, int Ns, int LG, int NT, int B, bool InPlace = false, class Dst>
 __device__ __forceinline__ void pair_pass(const float2 *src, const float2 *__restrict__ tw, const Dst &dst)
 {
     constexpr int PAIRS = (1 << LG) / 2, NB = N / R, TOTAL = PAIRS * NB;
     const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float2 lo[B][R], hi[B][R];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int idx = threadIdx.x + b * NT;
         if (B * NT == TOTAL || idx < TOTAL) {
             const int lp = idx % PAIRS, j = idx / PAIRS;
-            float2 lo[R], hi[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const float4 q = s4[(j + r * NB) * PAIRS + lp];
-                lo[r] = make_float2(q.x, q.y);
-                hi[r] = make_float2(q.z, q.w);
+                lo[b][r] = make_float2(q.x, q.y);
+                hi[b][r] = make_float2(q.z, q.w);
             }
             const int k = j % Ns;
             if (Ns > 1) {
@@ -221,15 +225,24 @@ __device__ __forceinline__ void pair_pass(const float2 *src, const float2 *__res
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
                     const float2 w = ldgc(t + r - 1);
-                    lo[r] = ctw<S>(lo[r], w);
-                    hi[r] = ctw<S>(hi[r], w);
+                    lo[b][r] = ctw<S>(lo[b][r], w);
+                    hi[b][r] = ctw<S>(hi[b][r], w);
                 }
             }
-            Dft<R, S, float2>::run(lo);
-            Dft<R, S, float2>::run(hi);
+            Dft<R, S, float2>::run(lo[b]);
+            Dft<R, S, float2>::run(hi[b]);
+        }
+    }
+    if constexpr (InPlace) __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int idx = threadIdx.x + b * NT;
+        if (B * NT == TOTAL || idx < TOTAL) {
+            const int lp = idx % PAIRS, j = idx / PAIRS;
+            const int k = j % Ns;
             const int o = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst(lp, o + r * Ns, lo[r], hi[r]);
+            for (int r = 0; r < R; ++r) dst(lp, o + r * Ns, lo[b][r], hi[b][r]);
         }
     }
 }
@@ -289,6 +302,47 @@ __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V
         constexpr int next = TwOff + (Ns > 1 ? Ns * (R - 1) : 0);
         pipe_passes<Sh, S, N, Ns * R, next, Q + 1, Split>(Seq<Rest...>{}, X, C, tw, out, mma);
     }
+}
+
+// Passes Seq<R, Rest...> after the first (Ns: the product of the radices
+// before them), all on the scratch tile C in place, the last one writing the
+// stage's output (complex64, no split).
+template <class Sh, int S, int N, int Ns, int TwOff, class Out, int R, int... Rest>
+__device__ __forceinline__ void scratch_passes(Seq<R, Rest...>, float2 *C, const float2 *tw, const Out &out)
+{
+    constexpr bool Global = sizeof...(Rest) == 0;
+    constexpr int LG = Sh::lg, NT = Sh::threads, B = Sh::covering(R);
+    if constexpr (Sh::pairs(R)) {
+        if constexpr (Global) pair_pass<R, S, N, Ns, LG, NT, B>(C, tw + TwOff, out.pair);
+        else pair_pass<R, S, N, Ns, LG, NT, B, true>(C, tw + TwOff, PairSmemOut<LG>{C});
+    } else {
+        const SmemRowsC<float2, LG> rows{C};
+        if constexpr (Global) radix_pass<R, S, false, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, rows, out.single);
+        else radix_pass<R, S, true, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, rows, rows);
+    }
+    if constexpr (sizeof...(Rest) > 0) {
+        __syncthreads();
+        scratch_passes<Sh, S, N, Ns * R, TwOff + (Ns > 1 ? Ns * (R - 1) : 0)>(Seq<Rest...>{}, C, tw, out);
+    }
+}
+
+// A complex64 tile of at least two passes whose load buffer X is released
+// after the first pass (X -> C), so that the next load into it can start
+// while the other passes run in place on C: `released` issues that load.
+template <class Sh, int S, int N, class Out, class Released, int R0, int... Rest>
+__device__ __forceinline__ void early_release_passes(Seq<R0, Rest...>, const float2 *X, float2 *C,
+                                                     const float2 *tw, const Out &out, const Released &released)
+{
+    static_assert(sizeof...(Rest) >= 1, "the first pass must not be the last");
+    constexpr int LG = Sh::lg, NT = Sh::threads, B = Sh::per_thread(R0);
+    if constexpr (Sh::pairs(R0))
+        pair_pass<R0, S, N, 1, LG, NT, B>(X, tw, PairSmemOut<LG>{C});
+    else
+        radix_pass<R0, S, false, NT, B>(N, 1, tw, Sh::lines, MapLineFastC<LG>{}, SmemRowsC<float2, LG>{const_cast<float2 *>(X)},
+                                        SmemRowsC<float2, LG>{C});
+    __syncthreads();
+    released();
+    scratch_passes<Sh, S, N, R0, 0>(Seq<Rest...>{}, C, tw, out);
 }
 
 // FP64 tile in float-float: the first pass converts the FP64 tile X (as the
@@ -361,23 +415,32 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
         }
     };
     auto out_col = [&](long long c) -> long long { return c < W ? c : -1; };
+    // Complex64 TMA tiles of two or more passes release their load buffer after
+    // the first pass, so two loads are in flight while the rest runs; otherwise
+    // the next tile's load is issued once this one has landed.
+    constexpr bool Early = TMA && !Split && sizeof(V) == 8 && P::npass >= 2;
 
     issue(t, 0);
+    if (Early && t + gridDim.x < ntiles) issue(t + gridDim.x, 1);
     for (int i = 0;; ++i) {
         const int b = i & 1;
+        const long long tn = t + gridDim.x;
         // wait for this tile; the barrier also retires every read of the other buffer
         if constexpr (TMA) {
             const bool ok = mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1));
             if (__syncthreads_or(!ok)) {
-                if (tid == 0) atomicExch(err, 1u);
+                if (tid == 0) {
+                    atomicExch(err, 1u);
+                    // the other buffer's load, if one was issued, must land before the CTA exits
+                    if (Early && tn < ntiles) mbar_wait_bounded(&bars[b ^ 1], (unsigned)(((i + 1) >> 1) & 1));
+                }
                 return;
             }
         } else {
             cp_async_wait<0>();
             __syncthreads();
         }
-        const long long tn = t + gridDim.x;
-        if (tn < ntiles) issue(tn, b ^ 1);   // next tile flies while this one is transformed
+        if (!Early && tn < ntiles) issue(tn, b ^ 1);   // next tile flies while this one is transformed
 
         const long long o = t / tiles_per_outer;
         const long long c0 = (t - o * tiles_per_outer) * LINES;
@@ -400,7 +463,15 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
                 done = pipe_df<Sh, S, N>(typename P::seq{}, buf0 + b * TILE, scratch, (const dcx *)twdf, tdf);
             }
         }
-        if (!done) pipe_passes<Sh, S, N, 1, 0, 0, Split>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to, mma);
+        if constexpr (Early) {
+            const float2 *x = reinterpret_cast<const float2 *>(buf0 + b * TILE);
+            early_release_passes<Sh, S, N>(typename P::seq{}, x, reinterpret_cast<float2 *>(scratch),
+                                           reinterpret_cast<const float2 *>(tw), to, [&] {
+                                               if (tn + gridDim.x < ntiles) issue(tn + gridDim.x, b);
+                                           });
+        } else if (!done) {
+            pipe_passes<Sh, S, N, 1, 0, 0, Split>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to, mma);
+        }
         if (tn >= ntiles) break;
         t = tn;
     }
@@ -544,6 +615,8 @@ __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
         tma_load_3d(buf0 + b * TILE_RP + (N / 2) * LW, &tmap, (int)(W + c0 - 1), 0, (int)o, &bars[b]);
     };
 
+    // The next tile's load is issued once this one has landed (the load buffer is not released
+    // after the first pass as in k_strided_pipe: that measured 3-5% slower on 512-point stages).
     issue(t, 0);
     for (int i = 0;; ++i) {
         const int b = i & 1;
@@ -672,6 +745,9 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
         }
     };
 
+    // The load buffer is not released early here (unlike k_strided_pipe): the six passes of a
+    // tile hide the next load already, and the in-place passes' extra barriers made the
+    // 512-point operator slower.
     issue(t, 0);
     for (int i = 0;; ++i) {
         const int b = i & 1;
