@@ -215,12 +215,16 @@ bool shape_strided(const StageDesc &d, long long outer, long long W, size_t elem
 
 // Contiguous stage: whole lines, about `target` complex points per CTA
 // (0: 4096 for complex64, 2048 for complex128; the autotuner may pick others).
+// even_lines: an even count where possible, so that every CTA's run of lines of
+// an odd number of complex64 elements starts 16-byte aligned (the c2r kernel
+// then stages it with 16-byte copies).
 bool shape_contig(const StageDesc &d, long long nlines, size_t elem, int max_threads, size_t max_smem,
-                  Launch &L, int target = 0)
+                  Launch &L, int target = 0, bool even_lines = false)
 {
     if (target <= 0) target = elem == 8 ? 4096 : 2048;
     int lines = std::max(1, target / std::max(1, d.n));
     lines = (int)std::min<long long>(lines, std::max(1LL, nlines));
+    if (even_lines && lines > 1 && (lines & 1)) --lines;
     const int row = (int)(128 / elem);
     for (;;) {
         const int thr = required_threads(d, lines);
@@ -392,7 +396,9 @@ int plan_shapes(afft_plan *p)
         const FourStep &f = p->four[a];
         AxisPlan &ap = p->ax[a];
         bool ok;
-        if (a == 2 && !f.on) ok = shape_contig(z.desc, B * n0 * n1, elem, z.ks->max_threads, budget(z), z.launch);
+        if (a == 2 && !f.on)
+            ok = shape_contig(z.desc, B * n0 * n1, elem, z.ks->max_threads, budget(z), z.launch, 0,
+                              p->kind == AFFT_R2C && (nh & 1));
         else ok = shape_strided(ap.desc, outer[a], width[a] * (f.on ? f.na : 1), elem, ap.ks->max_threads,
                                 budget(ap), ap.launch);
         if (!ok) return AFFT_ERR_UNSUPPORTED;
@@ -421,11 +427,16 @@ int plan_shapes(afft_plan *p)
 // --------------------------------------------------------------- execute ---
 
 // Shared memory of the c2r kernel: the work tile, then (specialised complex128
-// kernels) the tile's half spectra staged at M + 1 elements per line.
+// kernels) the tile's half spectra staged at M + 1 elements per line; specialised
+// complex64 kernels stage them in the work tile itself, so it holds
+// lines * (M + 1) elements.
 size_t c2r_smem(const AxisPlan &a, size_t elem)
 {
-    if (a.ks->generic || elem != 16) return a.launch.smem;
-    return a.launch.smem + (size_t)a.launch.lines * (a.desc.n + 1) * elem;
+    if (a.ks->generic) return a.launch.smem;
+    const size_t staged = (size_t)a.launch.lines * (a.desc.n + 1) * elem;
+    if (elem == 16) return a.launch.smem + staged;
+    if (a.desc.mma) return a.launch.smem;   // split precision: the first pass reads global memory
+    return std::max(a.launch.smem, (staged + 127) / 128 * 128);
 }
 
 cudaError_t launch(const AxisPlan &a, int which, long long blocks, void **args, cudaStream_t s)
@@ -858,7 +869,8 @@ bool reshape_contig(afft_plan *p, int target)
     AxisPlan &z = p->ax[2];
     const size_t budget = z.ks->generic ? (size_t)max_smem : (size_t)std::min(max_smem, 112 * 1024);
     Launch L;
-    if (!shape_contig(z.desc, p->batch * p->n[0] * p->n[1], sizeof(V), z.ks->max_threads, budget, L, target))
+    const bool even = p->kind == AFFT_R2C && ((p->n[2] / 2 + 1) & 1);
+    if (!shape_contig(z.desc, p->batch * p->n[0] * p->n[1], sizeof(V), z.ks->max_threads, budget, L, target, even))
         return false;
     z.launch = L;
     p->contig_target = target;

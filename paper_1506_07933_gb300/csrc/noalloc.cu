@@ -321,9 +321,12 @@ int run(const int64_t n[3], int precision, const void *in, void *out, cudaStream
         T sc = (T)scale;
         void *args[] = {(void *)&win, (void *)&o, (void *)&d, (void *)&twa, (void *)&post, (void *)&nlines,
                         (void *)&lines, (void *)&sc};
-        // specialised complex128 c2r kernels stage the tile's half spectra behind the work tile
-        const size_t smem = (a.ks->generic || sizeof(V) != 16) ? a.smem
-                                                               : a.smem + (size_t)a.lines * (a.d.n + 1) * sizeof(V);
+        // specialised c2r kernels stage the tile's half spectra: complex128 behind the work tile,
+        // complex64 in the work tile itself (lines * (M + 1) elements)
+        const size_t staged = (size_t)a.lines * (a.d.n + 1) * sizeof(V);
+        const size_t smem = a.ks->generic ? a.smem
+                            : sizeof(V) == 16 ? a.smem + staged
+                                              : (a.smem > (staged + 127) / 128 * 128 ? a.smem : (staged + 127) / 128 * 128);
         if (cudaLaunchKernel(a.ks->fn[KS_C2R], dim3((unsigned)a.blocks), dim3(a.threads), args, smem, s) !=
             cudaSuccess)
             return AFFT_ERR_CUDA;
