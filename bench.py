@@ -19,6 +19,7 @@ same workload, reported in the same unit.
 from __future__ import annotations
 
 import argparse
+import math
 import hashlib
 import json
 import os
@@ -308,6 +309,8 @@ def run_gpu(args):
         "roofline": roofline,
         "stages": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in kk.items()} for kk in kernels],
         "stage_ms_total": total_stage_ms,
+        # r2c + c2r of the field counted as 2 x 2.5 N log2 N flops, all GPUs
+        "gflops": world * 5.0 * math.prod(SHAPE) * math.log2(math.prod(SHAPE)) / (ms * 1e-3) / 1e9,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(t_begin, t_end),
@@ -507,12 +510,19 @@ def serving_workload(torch, count=400, rate=200.0, saturation=200, loaded=700.0)
     return out
 
 
+# FP64 FMA rate of one GB300 measured with 8 independent DFMA chains per thread (TFLOP/s): the
+# native FP64 roofline that the float-float FP64 transforms are set against
+NATIVE_FP64_TFLOPS = 1.26
+
+
 def extra_configs(afft, torch, peak):
-    """The other roofline configurations of the metric, fewer repetitions, same method."""
+    """The other roofline configurations of the metric, fewer repetitions, same method.  Each
+    entry also gives GFLOP/s by the usual count, 5 N log2 N per c2c transform and 2.5 N log2 N per
+    r2c or c2r, and FP64 entries their ratio to the native FP64 FMA rate."""
     out = []
     for shape, kind, prec in (((512,) * 3, "r2c", "f32"), ((512,) * 3, "r2c", "f64"), ((512,) * 3, "c2c", "f32"),
                               ((512,) * 3, "c2c", "f64"), ((1024,) * 3, "c2c", "f32"),
-                              ((1024,) * 3, "c2c", "f32_split")):
+                              ((1024,) * 3, "c2c", "f64"), ((1024,) * 3, "c2c", "f32_split")):
         p = afft.Plan(shape, kind, prec)
         x = torch.empty(p.spatial_shape, dtype=p.spatial_dtype, device="cuda")
         if kind == "c2c":
@@ -524,8 +534,7 @@ def extra_configs(afft, torch, peak):
         cb = 16 if prec == "f64" else 8
         rb = cb // 2
         if kind == "c2c":
-            N = shape[0] * shape[1] * shape[2]
-            b = 3 * 2 * N * cb
+            b = 3 * 2 * shape[0] * shape[1] * shape[2] * cb
         else:
             b = sum(workload_bytes(shape, rb, cb))
         for _ in range(3):
@@ -541,8 +550,14 @@ def extra_configs(afft, torch, peak):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        out.append({"workload": "%s %dx%dx%d %s fwd+bwd" % ((kind,) + shape + (prec,)), "ms_per_step": ms,
-                    "frac_of_hbm_roofline": 2 * b / (ms * 1e-3) / 1e9 / peak})
+        N = shape[0] * shape[1] * shape[2]
+        flops = 2 * (5.0 if kind == "c2c" else 2.5) * N * math.log2(N)   # forward + backward
+        entry = {"workload": "%s %dx%dx%d %s fwd+bwd" % ((kind,) + shape + (prec,)), "ms_per_step": ms,
+                 "frac_of_hbm_roofline": 2 * b / (ms * 1e-3) / 1e9 / peak,
+                 "gflops": flops / (ms * 1e-3) / 1e9}
+        if prec == "f64":
+            entry["vs_native_fp64_fma_peak"] = entry["gflops"] / (NATIVE_FP64_TFLOPS * 1e3)
+        out.append(entry)
         if kind == "r2c":
             # the fused spectral Poisson solve on the same field: 5 array passes (r2c N2, N1; fused
             # N0 forward / 1/|k|^2 / inverse; c2r N1, N2) against the 6 of forward + backward

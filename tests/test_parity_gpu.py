@@ -153,6 +153,18 @@ def test_r2c_odd_width_rows(shape):
            TOL["f32"])
 
 
+@pytest.mark.parametrize("shape", [(3, 2, 8192), (8, 10, 160), (4, 6, 500)])
+def test_c2r_staged_and_direct_tiles(shape):
+    """The specialised complex64 c2r kernels copy a CTA's run of half-spectrum lines into shared
+    memory when the run starts 16-byte aligned and read global memory otherwise.  One-line CTAs
+    of n2/2 = 4096 (4097 bins) alternate between the two; 81 bins (n2 = 160) take 50 of the 51
+    lines a CTA would hold, so every run is aligned; n2/2 = 250 runs the generic kernel."""
+    x = synth.uniform_real(shape, 41).astype(np.float32)
+    H = oracle.r2c(x).astype(np.complex64)
+    report("c2r staging %s f32" % (shape,), oracle.rel_l2(gpu_c2r(H, shape, "f32"), oracle.c2r(H, shape[2])),
+           TOL["f32"])
+
+
 def test_c2r_drops_imaginary_parts_of_self_conjugate_bins():
     shape = (4, 6, 16)
     H = oracle.r2c(synth.uniform_real(shape, 3))
