@@ -373,10 +373,10 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     using Sh = PipeShape<P, V>;
     constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
     constexpr unsigned TILE_BYTES = TILE * sizeof(V);
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    V *const buf0 = reinterpret_cast<V *>(smem_raw);   // load buffer b at buf0 + b * TILE
+    extern __shared__ __align__(1024) unsigned char pipe_smem_raw[];
+    V *const buf0 = reinterpret_cast<V *>(pipe_smem_raw);   // load buffer b at buf0 + b * TILE
     V *const scratch = buf0 + 2 * TILE;                  // out-of-place passes
-    unsigned long long *const bars = reinterpret_cast<unsigned long long *>(smem_raw + 3 * TILE_BYTES);
+    unsigned long long *const bars = reinterpret_cast<unsigned long long *>(pipe_smem_raw + 3 * TILE_BYTES);
     const int tid = threadIdx.x;
 
     long long t = blockIdx.x;
@@ -589,11 +589,11 @@ __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
     constexpr int N = P::n, LINES = Sh::lines, LW = Sh::lw, TILE_RP = Sh::tile_rp;
     constexpr unsigned BOX_BYTES = (N / 2) * LW * sizeof(V);
     static_assert(Sh::rp_ok, "row-pair tiles: 16 complex64 columns, n a multiple of 16, at most 512");
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    V *const buf0 = reinterpret_cast<V *>(smem_raw);   // load buffer b at buf0 + b * TILE_RP
+    extern __shared__ __align__(1024) unsigned char pipe_smem_raw[];
+    V *const buf0 = reinterpret_cast<V *>(pipe_smem_raw);   // load buffer b at buf0 + b * TILE_RP
     V *const scratch = buf0 + 2 * TILE_RP;
     unsigned long long *const bars =
-        reinterpret_cast<unsigned long long *>(smem_raw + (2 * TILE_RP + Sh::tile) * sizeof(V));
+        reinterpret_cast<unsigned long long *>(pipe_smem_raw + (2 * TILE_RP + Sh::tile) * sizeof(V));
     const int tid = threadIdx.x;
 
     long long t = blockIdx.x;
@@ -704,10 +704,10 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     using Sh = PipeShape<P, V>;
     constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
     constexpr unsigned TILE_BYTES = TILE * sizeof(V);
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    V *const buf0 = reinterpret_cast<V *>(smem_raw);
+    extern __shared__ __align__(1024) unsigned char pipe_smem_raw[];
+    V *const buf0 = reinterpret_cast<V *>(pipe_smem_raw);
     V *const scratch = buf0 + 2 * TILE;
-    unsigned long long *const bars = reinterpret_cast<unsigned long long *>(smem_raw + 3 * TILE_BYTES);
+    unsigned long long *const bars = reinterpret_cast<unsigned long long *>(pipe_smem_raw + 3 * TILE_BYTES);
     const int tid = threadIdx.x;
 
     long long t = blockIdx.x;

@@ -440,6 +440,40 @@ __device__ __forceinline__ void r2c_post(const Tile &tile, V *o, const CT *post_
     }
 }
 
+// r2c_post for a compile-time M when the CTA size is a multiple of M/2: thread
+// t owns the bin pair k = t mod M/2 (k and M - k) of lines t div M/2, +step,
+// ..., so its twiddle is loaded once and no index is divided; k = 0 also
+// writes X[M] and X[M/2] = conj Z[M/2] (E = Re Z, O = Im Z, w^{M/2} = -i).
+// Returns false, doing nothing, when the CTA size does not fit.
+template <int M, typename V, typename CT, class Tile>
+__device__ __forceinline__ bool r2c_post_fixed_k(const Tile &tile, V *o, const CT *post_tw, int ld, int valid)
+{
+    if constexpr (M < 2) {
+        return false;
+    } else {
+        using T = typename RealOf<CT>::T;
+        constexpr int H = M / 2;
+        const int nthr = blockDim.x;
+        if (H > nthr || nthr % H != 0) return false;
+        const int k = threadIdx.x % H;
+        const int step = nthr / H;
+        const CT w = ldgc(post_tw + k);
+        for (int l = threadIdx.x / H; l < valid; l += step) {
+            V *line = o + l * ld;
+            const CT zk = tile(l, k);
+            const CT zm = cconj(tile(l, k == 0 ? 0 : M - k));
+            const CT e = cscale(cadd(zk, zm), T(0.5));
+            const CT dd = csub(zk, zm);
+            const CT od = cmk<CT>(T(0.5) * dd.y, T(-0.5) * dd.x);  // (zk - zm) / (2i)
+            const CT t = cmul(od, w);
+            line[k] = Conv<CT, V>::out(cnorm(cadd(e, t)));
+            line[k == 0 ? M : M - k] = Conv<CT, V>::out(cnorm(cconj(csub(e, t))));
+            if (k == 0) line[H] = Conv<CT, V>::out(cnorm(cconj(tile(l, H))));
+        }
+        return true;
+    }
+}
+
 // Contiguous axis, real line of 2M points -> M+1 bins (forward).  The line is
 // read as M complex z[m] = x[2m] + i x[2m+1]; Z = DFT_M(z) is left in shared
 // memory and post-processed:
@@ -468,6 +502,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
             const SmemLines<dcx> tdf{reinterpret_cast<dcx *>(sm), M};
             if (df_stage<typename F::plan, -1, true>((const dcx *)d.twdf, lines, map, sdf, tdf, tdf, bad)) {
                 __syncthreads();
+                // (float-float tiles keep the general loop: the fixed-bin form measured no faster)
                 r2c_post<V, dcx>(tdf, o, (const dcx *)d.post_df, M, ld, valid);
                 return;
             }
@@ -478,6 +513,9 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     if constexpr (F::generic) run_generic<-1, false, true, F::split>(d, tw, sm, lines, 0, map, src, tile);
     else run_plan<typename F::plan, -1, true, F::split>(tw, lines, map, src, tile, tile, d.mma);
     __syncthreads();
+    if constexpr (!F::generic && sizeof(V) == 8) {
+        if (r2c_post_fixed_k<F::plan::n, V, V>(tile, o, post_tw, ld, valid)) return;
+    }
     r2c_post<V, V>(tile, o, post_tw, M, ld, valid);
     (void)sizeof(T);
 }
