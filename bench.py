@@ -321,6 +321,7 @@ def run_gpu(args):
 
     if args.extra and rank == 0:
         line["also"] = extra_configs(afft, torch, peak)
+        line["cufft"] = cufft_reference(torch, peak)
         line["batched"] = batched_workload(afft, torch)
         line["serving"] = serving_workload(torch)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -572,6 +573,47 @@ def extra_configs(afft, torch, peak):
                         "ms_fwd_plus_bwd": ms})
         del x, X, y
         p.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def cufft_reference(torch, peak):
+    """cuFFT (through torch.fft) on the same configurations, a reference baseline only: forward
+    unscaled and backward scaled by 1/N as in afft (rfftn / irfftn, fftn / ifftn).  Same timing
+    method and bytes as extra_configs."""
+    out = []
+    for shape, kind, dt in (((512,) * 3, "r2c", torch.float32), ((512,) * 3, "r2c", torch.float64),
+                            ((512,) * 3, "c2c", torch.complex64), ((512,) * 3, "c2c", torch.complex128),
+                            ((1024,) * 3, "c2c", torch.complex64), ((1024,) * 3, "c2c", torch.complex128)):
+        x = torch.empty(shape, dtype=dt, device="cuda")
+        if kind == "c2c":
+            x.real.uniform_(-1, 1)
+            x.imag.uniform_(-1, 1)
+            fwd = lambda: torch.fft.fftn(x)
+            bwd = lambda X: torch.fft.ifftn(X)
+            cb = 16 if dt == torch.complex128 else 8
+            b = 3 * 2 * math.prod(shape) * cb
+        else:
+            x.uniform_(-1, 1)
+            fwd = lambda: torch.fft.rfftn(x)
+            bwd = lambda X: torch.fft.irfftn(X, s=shape)
+            cb = 16 if dt == torch.float64 else 8
+            b = sum(workload_bytes(shape, cb // 2, cb))
+        for _ in range(3):
+            bwd(fwd())
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            bwd(fwd())
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        prec = {torch.float32: "f32", torch.float64: "f64", torch.complex64: "f32", torch.complex128: "f64"}[dt]
+        out.append({"workload": "cuFFT %s %dx%dx%d %s fwd+bwd" % ((kind,) + shape + (prec,)), "ms_per_step": ms,
+                    "frac_of_hbm_roofline": 2 * b / (ms * 1e-3) / 1e9 / peak})
+        del x
         torch.cuda.empty_cache()
     return out
 
