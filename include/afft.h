@@ -188,6 +188,27 @@ size_t afft_plan_input_bytes(const afft_plan *p);
 size_t afft_plan_output_bytes(const afft_plan *p);
 
 /*
+ * Blocked layout of c2c plans.  A c2c plan whose N0 rows lie more than 4 MB apart
+ * (1024^3 complex64) would make every tile of the N0 stage touch as many 2 MB pages
+ * as it has rows.  Such a plan instead runs its stages through a workspace that
+ * holds the array as [n1/32][batch*n0][32][n2]: the contiguous N2 stage writes
+ * its lines there, the N0 stage runs on rows 32*n2 complex apart, and the N1
+ * stage reads each column as n1/32 runs of 32 rows and writes `out` row-major
+ * (the paper's stage order, Algorithm 1, with the N0 and N1 stages swapped: the
+ * DFTs along different axes commute).  The backward transform runs the same
+ * stages in the same order and applies the 1/N in its first stage.
+ * afft_plan_create turns this on where it applies and the workspace fits;
+ * afft_plan_set_blocked(p, 1) turns it on for any plan whose shapes allow it
+ * (c2c, n0 >= 2, n1 a multiple of 32, no four-step axis, pipelined kernels for
+ * the n0 and n1 line lengths, a contiguous-stage CTA size dividing 32;
+ * AFFT_ERR_UNSUPPORTED otherwise, AFFT_ERR_NOMEM if the workspace cannot be
+ * allocated) and allocates the workspace (batch*n0*n1*n2 complex, counted by
+ * afft_plan_workspace_bytes); (p, 0) frees it and returns to row-major stages.
+ * Results differ only by rounding.  Not while the plan is in use on a stream.
+ */
+int afft_plan_set_blocked(afft_plan *p, int on);
+
+/*
  * L2-resident stage fusion.  The N2 and N1 stages can run slab by slab (a slab
  * is a range of N0 planes): the N2 stage of slab c, then the N1 stage of slab c
  * on a second stream the plan owns, while the N2 stage of slab c+1 runs, so the

@@ -42,6 +42,7 @@ EXPORTS = [
     "afft_plan_device_status", "afft_plan_set_l2_chunk", "afft_plan_l2_chunk",
     "afft_plan_create_batched", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
     "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe",
+    "afft_plan_set_blocked",
 ]
 
 _lib = None
@@ -89,6 +90,7 @@ def load(path: str = None):
     lib.afft_plan_device_status.argtypes = [vp]
     lib.afft_plan_wait_probe.argtypes = [vp, c_int, vp]
     lib.afft_plan_set_l2_chunk.argtypes = [vp, sz]
+    lib.afft_plan_set_blocked.argtypes = [vp, c_int]
     lib.afft_plan_l2_chunk.argtypes = [vp]
     lib.afft_plan_l2_chunk.restype = sz
     for f in ("afft_plan_create", "afft_plan_create_batched", "afft_execute_forward", "afft_execute_backward",
@@ -96,7 +98,8 @@ def load(path: str = None):
               "afft_plan_launches", "afft_fill_uniform", "afft_plan_timing_begin",
               "afft_plan_timing_end", "afft_c2r_noalloc", "afft_plan_device_status",
               "afft_plan_set_l2_chunk", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
-              "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe"):
+              "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe",
+              "afft_plan_set_blocked"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -279,6 +282,10 @@ class Plan:
                 raise ValueError("%s must be a contiguous CPU tensor %s %s" % (w, dt, shape))
         afft_execute_backward_host(self._p, host_in.data_ptr(), host_out.data_ptr(), dev_in.data_ptr(),
                                    dev_out.data_ptr(), _stream_handle(stream))
+
+    def set_blocked(self, on: bool) -> None:
+        """Blocked c2c layout (a workspace of the array's size; see afft_plan_set_blocked)."""
+        _check(load().afft_plan_set_blocked(self._p, int(bool(on))), "afft_plan_set_blocked")
 
     def set_l2_chunk(self, nbytes: int) -> None:
         """Slab size for L2-resident fusion of the N2 and N1 stages (0: unfused)."""

@@ -78,7 +78,21 @@ struct afft_plan {
     int chunk_planes;      // planes per slab; 0 when the stages run unfused
     cudaStream_t aux;
     std::vector<cudaEvent_t> chunk_ev;  // [0]: fork, then two per slab
+    // blocked layout of large c2c plans (see run_blocked): a workspace holding the array as
+    // [n1 / kBlk][batch * n0][kBlk][n2] and the tensor maps of the N0 and N1 stages over it
+    bool blk_eligible;     // the plan's shapes allow it
+    bool blocked;          // in use (workspace allocated, maps encoded)
+    void *d_blk;
+    size_t blk_bytes;
+    alignas(64) CUtensorMap blk_map0;   // N0 stage: [(n1 / kBlk) batch][n0][kBlk n2]
+    alignas(64) CUtensorMap blk_map1;   // N1 stage: [(n1 / kBlk) batch n0][kBlk][n2] boxes of kBlk rows
 };
+
+namespace {
+// Rows per block of the blocked c2c layout: an N0 column of the workspace has rows kBlk n2
+// complex apart (256 KB for n2 = 1024 complex64), an N1 column is n1 / kBlk runs of kBlk rows.
+constexpr int kBlk = 32;
+}
 
 namespace {
 
@@ -345,11 +359,16 @@ int plan_shapes(afft_plan *p)
         AxisPlan &ap = p->ax[a];
         ap.pipe = false;
         const KernelSet *ks = ap.ks;
+        ap.pipe_avail = false;
+        ap.pipe_slots = 0;
         if (ks->generic || !ks->pipe[PIPE_FWD_TMA] || ks->pipe_smem > max_smem) continue;
-        if (ks->n >= 1024 && row_bytes[a] > (1LL << 22)) continue;
         for (int k = 0; k < PIPE_COUNT; ++k)
             if (cudaFuncSetAttribute(ks->pipe[k], cudaFuncAttributeMaxDynamicSharedMemorySize, ks->pipe_smem) !=
                 cudaSuccess)
+                return AFFT_ERR_CUDA;
+        for (int k = 0; k < 2; ++k)
+            if (ks->pipe_blk[k] && cudaFuncSetAttribute(ks->pipe_blk[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        ks->pipe_smem) != cudaSuccess)
                 return AFFT_ERR_CUDA;
         for (int k = 0; k < 2; ++k)
             if (ks->poisson[k] && cudaFuncSetAttribute(ks->poisson[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -359,9 +378,11 @@ int plan_shapes(afft_plan *p)
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks->pipe[PIPE_FWD_TMA], ks->pipe_threads,
                                                           ks->pipe_smem) != cudaSuccess || per_sm < 1)
             continue;
-        ap.pipe_slots = sms * per_sm;
-        ap.pipe_avail = true;
-        ap.pipe = true;
+        ap.pipe_slots = sms * per_sm;   // also what the blocked c2c layout runs with
+        // rows far apart: the many CTAs of the plain kernel win in the row-major layout
+        const bool far = ks->n >= 1024 && row_bytes[a] > (1LL << 22);
+        ap.pipe_avail = !far;
+        ap.pipe = !far;
         ap.rp_slots = 0;
         if (ks->pipe_rp[0] && ks->pipe_smem_rp <= max_smem) {
             bool ok = true;
@@ -503,6 +524,47 @@ bool encode_strided_map(CUtensorMap *map, const void *base, long long outer, int
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The N1-stage map of the blocked c2c layout: a [zdim][rows][W] array (W complex of C bytes)
+// read in boxes of `lines` columns x `rows` rows.
+bool encode_blocked_map(CUtensorMap *map, const void *base, long long zdim, int rows, long long W, size_t C,
+                        int lines)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const size_t per = C / 8;
+    if ((W * C) % 16 != 0 || ((uintptr_t)base) % 16 != 0 || W < lines || rows < 1 || rows > 256) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)(W * per), (cuuint64_t)rows, (cuuint64_t)zdim};
+    cuuint64_t strides[2] = {(cuuint64_t)(W * C), (cuuint64_t)(rows * W * C)};
+    cuuint32_t box[3] = {(cuuint32_t)(lines * per), (cuuint32_t)rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The pipelined kernel over a [outer][n][W] stage whose tiles load through `map` (TMA) or
+// from `in` (cp.async); zrows > 0: the map holds each line's rows as blocks of zrows rows,
+// block k of outer line o at z = k zstride + o (the blocked c2c layout).
+template <typename V>
+cudaError_t pipe_on_map(const AxisPlan &a, const CUtensorMap &map, bool tma, const V *in, V *out, const V *tw,
+                        long long outer, long long W, int backward, unsigned *err, int zrows, long long zstride,
+                        cudaStream_t s)
+{
+    const int which = backward ? (tma ? PIPE_BWD_TMA : PIPE_BWD_CPASYNC) : (tma ? PIPE_FWD_TMA : PIPE_FWD_CPASYNC);
+    const void *fn = zrows > 0 ? a.ks->pipe_blk[backward ? 1 : 0] : a.ks->pipe[which];
+    if (zrows > 0 && (!tma || !fn)) return cudaErrorInvalidValue;
+    tw += a.tw_base;
+    long long tpo = (W + a.ks->pipe_lines - 1) / a.ks->pipe_lines;
+    long long nt = outer * tpo;
+    const void *twdf = a.desc.twdf;
+    const unsigned *mma = a.desc.mma;
+    const unsigned grid = (unsigned)std::min<long long>(nt, a.pipe_slots);
+    void *args[] = {(void *)&in,   (void *)&out, (void *)&map, (void *)&tw,    (void *)&W,      (void *)&tpo,
+                    (void *)&nt,   (void *)&err, (void *)&twdf, (void *)&mma, (void *)&zrows, (void *)&zstride};
+    if (nt <= 0 || grid == 0) return nt <= 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+    return cudaLaunchKernel(fn, dim3(grid), dim3(a.ks->pipe_threads), args, (size_t)a.ks->pipe_smem, s);
+}
+
 template <typename V>
 cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, long long outer, long long W,
                          int backward, unsigned *err, cudaStream_t s)
@@ -524,17 +586,7 @@ cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, lo
                                 (size_t)a.ks->pipe_smem_rp, s);
     }
     const bool tma = encode_strided_map(&map, in, outer, a.desc.n, W, sizeof(V), a.ks->pipe_lines);
-    const int which = backward ? (tma ? PIPE_BWD_TMA : PIPE_BWD_CPASYNC) : (tma ? PIPE_FWD_TMA : PIPE_FWD_CPASYNC);
-    tw += a.tw_base;
-    long long tpo = (W + a.ks->pipe_lines - 1) / a.ks->pipe_lines;
-    long long nt = outer * tpo;
-    const void *twdf = a.desc.twdf;
-    const unsigned *mma = a.desc.mma;
-    const unsigned grid = (unsigned)std::min<long long>(nt, a.pipe_slots);
-    void *args[] = {(void *)&in, (void *)&out, (void *)&map, (void *)&tw,   (void *)&W,
-                    (void *)&tpo, (void *)&nt, (void *)&err, (void *)&twdf, (void *)&mma};
-    return cudaLaunchKernel(a.ks->pipe[which], dim3(grid), dim3(a.ks->pipe_threads), args,
-                            (size_t)a.ks->pipe_smem, s);
+    return pipe_on_map<V>(a, map, tma, in, out, tw, outer, W, backward, err, 0, 0, s);
 }
 
 // A strided stage over a [outer][n][W] array (in place when in == out).
@@ -636,6 +688,106 @@ cudaError_t axis_stage(afft_plan *p, int a, const V *in, V *out, long long outer
     return fourstep<V>(f, tmp, out, tw, outer, W, backward, scale, s);
 }
 
+// ------------------------------------------------------ blocked c2c layout ---
+// A c2c plan whose N0 rows lie more than 4 MB apart (1024^3 complex64: 8 MB) makes every
+// 1024-row tile of the N0 stage touch 1024 different 2 MB pages; that stage then runs at
+// about half the bandwidth of the others, bound by address translation.  Such plans run the
+// three stages through a workspace holding the array as [n1 / kBlk][B n0][kBlk][n2]:
+//   N2 stage   in -> workspace, each line to its blocked place (the CTA's lines stay
+//              consecutive: its line count divides kBlk);
+//   N0 stage   in place on the workspace, a [(n1 / kBlk) B][n0][kBlk n2] view: rows kBlk n2
+//              complex apart, kBlk rows per 2 MB page for n2 = 1024 complex64;
+//   N1 stage   workspace -> out, each column read as n1 / kBlk TMA boxes of kBlk rows
+//              (block k of plane o at z = k B n0 + o), written row-major.
+// The backward transform runs the same kernels in the same order, the N2 stage applying the
+// 1/N.  DFTs along different axes commute, so the order changes only rounding.
+
+// Whether the plan's shapes allow the blocked layout (not whether it is worth it).
+bool blocked_eligible(const afft_plan *p)
+{
+    if (p->kind != AFFT_C2C || p->n[0] < 2) return false;
+    for (int a = 0; a < 3; ++a)
+        if (p->four[a].on) return false;
+    const AxisPlan &x = p->ax[0], &y = p->ax[1], &z = p->ax[2];
+    if (x.pipe_slots <= 0 || y.pipe_slots <= 0 || !y.ks->pipe_blk[0] || p->n[1] % kBlk != 0) return false;
+    if (z.launch.lines < 1 || kBlk % z.launch.lines != 0) return false;
+    const size_t C = cplx_size(p->precision);
+    return (p->n[2] * (long long)C) % 16 == 0 && p->n[2] >= y.ks->pipe_lines;
+}
+
+// Allocates the workspace and encodes the two maps (on), or frees them (off).
+int set_blocked(afft_plan *p, bool on)
+{
+    if (!on) {
+        if (p->d_blk) cudaFree(p->d_blk);
+        p->d_blk = nullptr;
+        p->work_bytes -= p->blk_bytes;
+        p->blk_bytes = 0;
+        p->blocked = false;
+        return AFFT_OK;
+    }
+    if (p->blocked) return AFFT_OK;
+    if (!blocked_eligible(p)) return AFFT_ERR_UNSUPPORTED;
+    const size_t C = cplx_size(p->precision);
+    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], P0 = p->batch * n0;
+    const size_t bytes = (size_t)P0 * n1 * n2 * C;
+    if (cudaMalloc(&p->d_blk, bytes) != cudaSuccess) {
+        p->d_blk = nullptr;
+        cudaGetLastError();
+        return AFFT_ERR_NOMEM;
+    }
+    std::memset(&p->blk_map0, 0, sizeof p->blk_map0);
+    std::memset(&p->blk_map1, 0, sizeof p->blk_map1);
+    const bool ok =
+        encode_strided_map(&p->blk_map0, p->d_blk, (n1 / kBlk) * p->batch, (int)n0, kBlk * n2, C,
+                           p->ax[0].ks->pipe_lines) &&
+        encode_blocked_map(&p->blk_map1, p->d_blk, (n1 / kBlk) * P0, kBlk, n2, C, p->ax[1].ks->pipe_lines);
+    if (!ok) {
+        cudaFree(p->d_blk);
+        p->d_blk = nullptr;
+        return AFFT_ERR_UNSUPPORTED;
+    }
+    p->blk_bytes = bytes;
+    p->work_bytes += bytes;
+    p->blocked = true;
+    return AFFT_OK;
+}
+
+// Forward or backward transform through the blocked layout (see above).
+template <typename V>
+int run_blocked(afft_plan *p, const void *in, void *out, int backward, cudaStream_t s)
+{
+    const V *tw = (const V *)p->d_tw;
+    const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], P0 = p->batch * n0;
+    V *ws = (V *)p->d_blk;
+    AxisPlan z = p->ax[2];   // the N2 stage writes its lines to their blocked places
+    z.desc.blk = kBlk;
+    z.desc.blk_in = 0;
+    z.desc.blk_out = 1;
+    z.desc.blk_n1 = n1;
+    z.desc.blk_planes = P0;
+    const double scale = backward ? 1.0 / ((double)n0 * (double)n1 * (double)n2) : 1.0;
+    mark(p, 0, s);
+    if (contig<V>(z, (const V *)in, ws, tw, P0 * n1, backward, scale, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    mark(p, 1, s);
+    if (pipe_on_map<V>(p->ax[0], p->blk_map0, true, ws, ws, tw, (n1 / kBlk) * p->batch, kBlk * n2, backward,
+                       p->d_err, 0, 0, s) != cudaSuccess)
+        return AFFT_ERR_CUDA;
+    mark(p, 2, s);
+    if (pipe_on_map<V>(p->ax[1], p->blk_map1, true, ws, (V *)out, tw, P0, n2, backward, p->d_err, kBlk, P0, s) !=
+        cudaSuccess)
+        return AFFT_ERR_CUDA;
+    mark(p, 3, s);
+    return AFFT_OK;
+}
+
+// The blocked layout runs when it is set up and the current shapes still allow it (the
+// autotuner may pick a contiguous CTA size or an L2 slab schedule that do not).
+bool use_blocked(const afft_plan *p)
+{
+    return p->blocked && p->chunk_planes == 0 && blocked_eligible(p);
+}
+
 // Forward: N2 stage (c2c, or r2c), N1 stage, N0 stage, all writing `out`.
 // With chunk_planes > 0 the N2 and N1 stages run slab by slab: N2 of slab c on
 // the caller's stream, N1 of slab c on the plan's second stream right after, so
@@ -644,6 +796,7 @@ cudaError_t axis_stage(afft_plan *p, int a, const V *in, V *out, long long outer
 template <typename V>
 int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
+    if (use_blocked(p)) return run_blocked<V>(p, in, out, 0, s);
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
     const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, B = p->batch;
@@ -700,6 +853,7 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 template <typename V>
 int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
+    if (use_blocked(p)) return run_blocked<V>(p, in, out, 1, s);
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
     const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, B = p->batch;
@@ -1028,6 +1182,11 @@ int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch,
             st = AFFT_ERR_NOMEM;
         }
     }
+    if (st == AFFT_OK && blocked_eligible(p) && p->ax[0].ks->n >= 1024 &&
+        p->n[1] * p->n[2] * (long long)cplx_size(precision) > (1LL << 22)) {
+        // N0 rows beyond 4 MB apart: the blocked layout, when its workspace fits (else row-major)
+        if (set_blocked(p, true) != AFFT_OK) cudaGetLastError();
+    }
     if (st != AFFT_OK) {
         cudaGetLastError();  // clear a sticky launch error from the failed step
         afft_plan_destroy(p);
@@ -1102,8 +1261,9 @@ int afft_plan_destroy(afft_plan *p)
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
     int st = AFFT_OK;
-    if (p->d_tw || p->d_work || p->d_err || p->d_four || p->d_twdf || p->d_mma) {
+    if (p->d_tw || p->d_work || p->d_err || p->d_four || p->d_twdf || p->d_mma || p->d_blk) {
         if (cudaDeviceSynchronize() != cudaSuccess) st = AFFT_ERR_CUDA;
+        if (p->d_blk) cudaFree(p->d_blk);
         if (p->d_tw) cudaFree(p->d_tw);
         if (p->d_twdf) cudaFree(p->d_twdf);
         if (p->d_work) cudaFree(p->d_work);
@@ -1298,14 +1458,14 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         "{\"n\": [%lld, %lld, %lld], \"batch\": %lld, \"kind\": \"%s\", \"precision\": \"%s\", "
         "\"radix\": [\"%s\", \"%s\", \"%s\"], \"specialised\": [%d, %d, %d], \"four_step\": [%d, %d, %d], "
         "\"pipelined\": [%d, %d], \"contig_lines\": %d, \"strided_lines\": [%d, %d], "
-        "\"l2_slab_planes\": %d}",
+        "\"l2_slab_planes\": %d, \"blocked\": %d}",
         (long long)p->n[0], (long long)p->n[1], (long long)p->n[2], (long long)p->batch,
         p->kind == AFFT_C2C ? "c2c" : "r2c",
         p->precision == AFFT_F64 ? "f64" : p->precision == AFFT_F32_SPLIT ? "f32split" : "f32", radix[0], radix[1], radix[2],
         !p->ax[0].ks->generic, !p->ax[1].ks->generic, !p->ax[2].ks->generic, p->four[0].on, p->four[1].on,
         p->four[2].on, p->ax[0].pipe, p->ax[1].pipe, p->ax[2].launch.lines,
         p->ax[0].pipe ? p->ax[0].ks->pipe_lines : p->ax[0].launch.lines,
-        p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, p->chunk_planes);
+        p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, p->chunk_planes, (int)use_blocked(p));
     if (need < 0) return AFFT_ERR_CUDA;
     return (size_t)need < len ? AFFT_OK : AFFT_ERR_SIZE;
 }
@@ -1324,6 +1484,12 @@ int afft_plan_launches(const afft_plan *p, int backward)
     if (backward) return (int)(1 + f0 + slabs * (1 + f2 + y));
     const int x = p->n[0] > 1 ? 1 + f0 : 0;
     return (int)(slabs * (1 + f2 + y) + x);
+}
+
+int afft_plan_set_blocked(afft_plan *p, int on)
+{
+    if (!p) return AFFT_ERR_NULL;
+    return set_blocked(p, on != 0);
 }
 
 int afft_plan_set_l2_chunk(afft_plan *p, size_t bytes)

@@ -34,7 +34,19 @@ struct StageDesc {
     // split-precision plans: the tensor-core fragments of the 16-point DFT matrix
     // (both directions, see fft_split.cuh), else null
     const unsigned *mma;
+    // contiguous c2c stage of a blocked plan: the lines of `in` (blk_in) or of `out` (blk_out)
+    // lie in the layout [n1 / blk][planes][blk][n], line q = plane * n1 + j at line
+    // ((j / blk) * planes + plane) * blk + j % blk; blk = 0: row-major on both sides
+    int blk, blk_in, blk_out;
+    long long blk_n1, blk_planes;
 };
+
+// Line of the blocked layout holding row-major line q (see StageDesc::blk).
+__host__ __device__ inline long long blocked_line(const StageDesc &d, long long q)
+{
+    const long long pl = q / d.blk_n1, j = q - pl * d.blk_n1;
+    return ((j / d.blk) * d.blk_planes + pl) * d.blk + j % d.blk;
+}
 
 // Butterflies a thread carries per pass for radix R: at most 16 complex
 // values in registers (15 for radix 3 and 5).  The host picks the thread
@@ -79,10 +91,14 @@ enum { KS_STRIDED_FWD = 0, KS_STRIDED_BWD, KS_CONTIG_FWD, KS_CONTIG_BWD, KS_R2C,
 // Pipelined strided kernels (persistent CTAs, double-buffered tiles), indexed
 // by PIPE_*.  Signature: (const V *in, V *out, CUtensorMap map, const V *tw,
 // long long W, long long tiles_per_outer, long long ntiles, unsigned *err,
-// const void *twdf, const unsigned *mma) (twdf: the float-float twiddles of an
-// FP64 plan, or null; mma: the tensor-core DFT-16 table of a split-precision
-// plan, or null); the TMA variants read through `map`, the cp.async ones
-// through `in`.
+// const void *twdf, const unsigned *mma, int zrows, long long zstride) (twdf:
+// the float-float twiddles of an FP64 plan, or null; mma: the tensor-core
+// DFT-16 table of a split-precision plan, or null); the TMA variants read
+// through `map`, a [outer][n][W] view, the cp.async ones through `in`; zrows
+// and zstride are read only by the blocked variants (pipe_blk, TMA): there the
+// rows of outer line o are blocks of zrows rows, block k at z = k * zstride + o
+// of a [..][zrows][W] map.  The row-pair kernels (pipe_rp) take the first ten
+// of these arguments.
 enum { PIPE_FWD_TMA = 0, PIPE_FWD_CPASYNC, PIPE_BWD_TMA, PIPE_BWD_CPASYNC, PIPE_COUNT };
 
 struct KernelSet {
@@ -93,6 +109,7 @@ struct KernelSet {
     int max_threads;               // largest CTA the kernels were compiled for
     bool generic;
     const void *pipe[PIPE_COUNT];  // null when the family has no pipelined strided kernel
+    const void *pipe_blk[2];       // its blocked-row TMA variants ([0] forward, [1] backward)
     // generic family only: second half of a four-step line, (const V *in, V *out,
     // StageDesc d, const V *tw, const V *wn, long long W, long long tiles_per_outer,
     // int log2_lines, int nb, T scale); [0] forward, [1] backward
@@ -108,7 +125,7 @@ struct KernelSet {
     int pipe_threads;              // its (compile-time) CTA size
     int pipe_smem;                 // its dynamic shared memory (two tile buffers)
     // complex64 families: the pipelined kernels for rows of odd width, read as row pairs
-    // through TMA ([0] forward, [1] backward; same arguments as pipe[], see
+    // through TMA ([0] forward, [1] backward; the first ten arguments of pipe[], see
     // k_strided_pipe_rp) and their shared memory; null / 0 elsewhere
     const void *pipe_rp[2];
     int pipe_smem_rp;

@@ -364,11 +364,11 @@ __device__ __forceinline__ bool pipe_df(Seq<R0, Rest...>, double2 *X, double2 *C
 
 // ---------------------------------------------------------------- kernel ---
 
-template <class P, int S, typename V, bool TMA, bool Split = false>
+template <class P, int S, typename V, bool TMA, bool Split = false, bool Blocked = false>
 __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     k_strided_pipe(const V *__restrict__ in, V *out, const __grid_constant__ CUtensorMap tmap,
                    const V *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
-                   unsigned *err, const void *twdf, const unsigned *mma)
+                   unsigned *err, const void *twdf, const unsigned *mma, int zrows, long long zstride)
 {
     using Sh = PipeShape<P, V>;
     constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
@@ -397,9 +397,16 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
                 mbar_expect_tx(&bars[b], TILE_BYTES);
                 constexpr int rows = Sh::box_rows;
                 constexpr int per = (int)sizeof(V) / 8;  // 8-byte elements per complex value
+                if constexpr (Blocked) {
+                    // blocked rows: block k (rows k zrows ..) of line o is the box at z = k zstride + o
+                    for (int r0 = 0, k = 0; r0 < N; r0 += zrows, ++k)
+                        tma_load_3d(buf0 + b * TILE + r0 * LINES, &tmap, (int)(c0 * per), 0,
+                                    (int)(k * zstride + o), &bars[b]);
+                } else {
 #pragma unroll
-                for (int r0 = 0; r0 < N; r0 += rows)
-                    tma_load_3d(buf0 + b * TILE + r0 * LINES, &tmap, (int)(c0 * per), r0, (int)o, &bars[b]);
+                    for (int r0 = 0; r0 < N; r0 += rows)
+                        tma_load_3d(buf0 + b * TILE + r0 * LINES, &tmap, (int)(c0 * per), r0, (int)o, &bars[b]);
+                }
             }
         } else {
             const V *src = in + o * (long long)N * W + c0;
@@ -835,6 +842,8 @@ template <class F, typename V> KernelSet kernel_set(int n, int npass, const int 
             k.pipe[PIPE_FWD_CPASYNC] = (const void *)k_strided_pipe<P, -1, V, false, F::split>;
             k.pipe[PIPE_BWD_TMA] = (const void *)k_strided_pipe<P, +1, V, true, F::split>;
             k.pipe[PIPE_BWD_CPASYNC] = (const void *)k_strided_pipe<P, +1, V, false, F::split>;
+            k.pipe_blk[0] = (const void *)k_strided_pipe<P, -1, V, true, F::split, true>;
+            k.pipe_blk[1] = (const void *)k_strided_pipe<P, +1, V, true, F::split, true>;
             if constexpr (!F::split) {   // split plans run the Poisson multiply as its own kernel
                 k.poisson[0] = (const void *)k_poisson_pipe<P, V, true>;
                 k.poisson[1] = (const void *)k_poisson_pipe<P, V, false>;

@@ -355,8 +355,13 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     const int n = F::generic ? d.n : F::plan::n;
     const long long b0 = (long long)blockIdx.x * lines;
     const int valid = (int)min((long long)lines, nlines - b0);
-    const GlobalLines<V> src{in + b0 * n, n, valid};
-    const GlobalLinesOut<V> dst{out + b0 * n, n, valid, scale};
+    // a blocked layout on either side keeps the CTA's lines consecutive (the host makes `lines`
+    // divide the block), so only the first line's position changes
+    const long long lb = d.blk ? blocked_line(d, b0) : b0;
+    const V *in0 = in + (d.blk && d.blk_in ? lb : b0) * n;
+    V *out0 = out + (d.blk && d.blk_out ? lb : b0) * n;
+    const GlobalLines<V> src{in0, n, valid};
+    const GlobalLinesOut<V> dst{out0, n, valid, scale};
     const MapButterflyFast map{};
     if constexpr (F::generic) {
         run_generic<S, false, false, F::split>(d, tw, sm, lines, 0, map, src, dst);
@@ -364,8 +369,8 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
         if constexpr (UseDf<F, V>::value) {
             if (d.twdf) {
                 DfFlags bad;
-                const GlobalLines<V, dcx> sdf{in + b0 * n, n, valid, &bad};
-                const GlobalLinesOut<V, dcx> ddf{out + b0 * n, n, valid, dfl(scale)};
+                const GlobalLines<V, dcx> sdf{in0, n, valid, &bad};
+                const GlobalLinesOut<V, dcx> ddf{out0, n, valid, dfl(scale)};
                 const SmemLines<dcx> tdf{reinterpret_cast<dcx *>(sm), n};
                 if (df_stage<typename F::plan, S, false>((const dcx *)d.twdf, lines, map, sdf, tdf, ddf, bad)) return;
             }

@@ -633,3 +633,70 @@ def test_poisson_batched():
         torch.cuda.synchronize()
     for b in range(B):
         report("poisson batched [%d]" % b, oracle.rel_l2(got[b].cpu().numpy(), us[b]), 2e-6)
+
+
+# --- blocked c2c layout ([n1/32][batch n0][32][n2] workspace) --------------------------
+
+@pytest.mark.parametrize("shape,batch,prec", [((64, 64, 256), 1, "f32"), ((32, 96, 128), 1, "f32"),
+                                              ((16, 64, 128), 3, "f32"), ((64, 32, 128), 1, "f64"),
+                                              ((512, 32, 128), 1, "f32"), ((24, 64, 1024), 2, "f64")])
+def test_c2c_blocked_layout_matches_oracle(shape, batch, prec):
+    """The blocked layout (N2 stage into the workspace, N0 stage on rows 32 n2 apart, N1 stage
+    reading runs of 32 rows back to row-major) gives the oracle's transform, forward and back."""
+    xs = np.stack([synth.uniform_complex(shape, 90 + b) for b in range(batch)]).astype(CDT[prec])
+    with afft.Plan(shape, "c2c", prec, batch=batch if batch > 1 else None) as p:
+        p.set_blocked(True)
+        assert p.describe()["blocked"] == 1
+        n = int(np.prod(shape)) * batch
+        assert afft.load().afft_plan_workspace_bytes(p._p) >= n * np.dtype(CDT[prec]).itemsize
+        t = torch.from_numpy(xs if batch > 1 else xs[0]).cuda()
+        before = t.clone()
+        X = p.forward(t)
+        y = p.backward(X)
+        torch.cuda.synchronize()
+        assert torch.equal(t, before), "the blocked forward modified its input"
+        Xh = X.cpu().numpy().reshape((batch,) + shape)
+        yh = y.cpu().numpy().reshape((batch,) + shape)
+    for b in range(batch):
+        ref = oracle.c2c(xs[b], -1, "fft")
+        report("blocked c2c %s %s fwd [%d]" % (shape, prec, b), oracle.rel_l2(Xh[b], ref), TOL[prec])
+        report("blocked c2c %s %s round trip [%d]" % (shape, prec, b), oracle.rel_l2(yh[b], xs[b]), TOL[prec])
+
+
+def test_c2c_blocked_backward_alone_matches_oracle():
+    shape = (64, 64, 256)
+    X = synth.uniform_complex(shape, 95).astype(np.complex64)
+    with afft.Plan(shape, "c2c", "f32") as p:
+        p.set_blocked(True)
+        y = p.backward(torch.from_numpy(X).cuda())
+        torch.cuda.synchronize()
+    report("blocked c2c %s backward" % (shape,), oracle.rel_l2(y.cpu().numpy(), oracle.c2c(X, +1, "fft")), TOL["f32"])
+
+
+def test_c2c_blocked_split_precision():
+    shape = (32, 64, 256)
+    x = synth.uniform_complex(shape, 97).astype(np.complex64)
+    with afft.Plan(shape, "c2c", "f32_split") as p:
+        p.set_blocked(True)
+        X = p.forward(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+    report("blocked c2c %s split fwd" % (shape,), oracle.rel_l2(X.cpu().numpy(), oracle.c2c(x, -1, "fft")), 2e-5)
+
+
+def test_blocked_layout_eligibility_and_default():
+    """Refused where the shapes do not allow it; on by default where N0 rows lie beyond 4 MB
+    apart (1024^3 complex64: the plan's workspace is the array's size); off again on request."""
+    with afft.Plan((64, 64, 256), "r2c", "f32") as p:
+        with pytest.raises(afft.AfftError):
+            p.set_blocked(True)
+    with afft.Plan((64, 48, 256), "c2c", "f32") as p:   # n1 not a multiple of 32
+        with pytest.raises(afft.AfftError):
+            p.set_blocked(True)
+    with afft.Plan((512, 512, 512), "c2c", "f32") as p:  # N0 rows 2 MB apart: row-major
+        assert p.describe()["blocked"] == 0
+    with afft.Plan((1024, 1024, 1024), "c2c", "f32") as p:
+        assert p.describe()["blocked"] == 1
+        assert afft.load().afft_plan_workspace_bytes(p._p) == 1024 ** 3 * 8
+        p.set_blocked(False)
+        assert p.describe()["blocked"] == 0
+        assert afft.load().afft_plan_workspace_bytes(p._p) == 0
