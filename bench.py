@@ -267,6 +267,9 @@ def run_gpu(args):
         t_end = time.time()
     ms = e0.elapsed_time(e1) / args.steps
     stage = plan.timing_end()
+    # accuracy of the last timed step (outside the timed region): backward(forward(x)) against x
+    xd = x.double()
+    round_trip = float(torch.linalg.vector_norm(y.double() - xd) / torch.linalg.vector_norm(xd))
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -309,6 +312,7 @@ def run_gpu(args):
         "roofline": roofline,
         "stages": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in kk.items()} for kk in kernels],
         "stage_ms_total": total_stage_ms,
+        "round_trip_rel_l2": round_trip,
         # r2c + c2r of the field counted as 2 x 2.5 N log2 N flops, all GPUs
         "gflops": world * 5.0 * math.prod(SHAPE) * math.log2(math.prod(SHAPE)) / (ms * 1e-3) / 1e9,
         "e2e": e2e,

@@ -238,6 +238,19 @@ size_t afft_plan_l2_chunk(const afft_plan *p);
 int afft_plan_tune(afft_plan *p, void *cuda_stream);
 
 /*
+ * The autotuner's choices, to store and apply again (the Python binding keeps
+ * them in a cache file keyed by shape, kind, precision, batch and GPU):
+ * cfg[0] points per CTA of the contiguous stage (0: the default), cfg[1] and
+ * cfg[2] pipelined (1) or plain (0) kernels for the N0 and N1 stages, cfg[3]
+ * the L2 slab size in bytes (0: unfused).  set returns AFFT_ERR_UNSUPPORTED
+ * for a pipelined stage or a CTA size this plan cannot use, AFFT_ERR_SIZE for
+ * a negative value; it allocates nothing on the device.  Not while the plan
+ * is in use on a stream.
+ */
+int afft_plan_get_tuning(const afft_plan *p, int64_t cfg[4]);
+int afft_plan_set_tuning(afft_plan *p, const int64_t cfg[4]);
+
+/*
  * Writes a one-line JSON description of the plan's configuration (radix
  * sequences per axis, kernel families, four-step splits, pipelined stages,
  * lines per CTA, padded row pitch, L2 slab) into buf (NUL-terminated).

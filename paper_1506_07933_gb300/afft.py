@@ -42,7 +42,7 @@ EXPORTS = [
     "afft_plan_device_status", "afft_plan_set_l2_chunk", "afft_plan_l2_chunk",
     "afft_plan_create_batched", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
     "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe",
-    "afft_plan_set_blocked",
+    "afft_plan_set_blocked", "afft_plan_get_tuning", "afft_plan_set_tuning",
 ]
 
 _lib = None
@@ -91,6 +91,8 @@ def load(path: str = None):
     lib.afft_plan_wait_probe.argtypes = [vp, c_int, vp]
     lib.afft_plan_set_l2_chunk.argtypes = [vp, sz]
     lib.afft_plan_set_blocked.argtypes = [vp, c_int]
+    lib.afft_plan_get_tuning.argtypes = [vp, i64p]
+    lib.afft_plan_set_tuning.argtypes = [vp, i64p]
     lib.afft_plan_l2_chunk.argtypes = [vp]
     lib.afft_plan_l2_chunk.restype = sz
     for f in ("afft_plan_create", "afft_plan_create_batched", "afft_execute_forward", "afft_execute_backward",
@@ -99,7 +101,7 @@ def load(path: str = None):
               "afft_plan_timing_end", "afft_c2r_noalloc", "afft_plan_device_status",
               "afft_plan_set_l2_chunk", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
               "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe",
-              "afft_plan_set_blocked"):
+              "afft_plan_set_blocked", "afft_plan_get_tuning", "afft_plan_set_tuning"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -295,9 +297,33 @@ class Plan:
     def l2_chunk(self) -> int:
         return int(load().afft_plan_l2_chunk(self._p))
 
-    def tune(self, stream=None) -> None:
-        """Autotune the launch configuration on temporary buffers (synchronises)."""
+    def tune(self, stream=None, cache: str = None) -> bool:
+        """Autotune the launch configuration on temporary buffers (synchronises).  With `cache`
+        (a JSON file), a choice stored there for this plan's key (shape, kind, precision, batch,
+        GPU name) is applied instead of tuning, and a new one is stored.  Returns True when the
+        choice came from the cache."""
+        key = tuning_key(self.shape, self.kind, self.precision, self.batch,
+                         torch.cuda.get_device_name(self.device)) if cache else None
+        if cache:
+            cfg = tuning_cache_lookup(cache, key)
+            if cfg is not None:
+                self.set_tuning(cfg)
+                return True
         _check(load().afft_plan_tune(self._p, _stream_handle(stream)), "afft_plan_tune")
+        if cache:
+            tuning_cache_store(cache, key, self.tuning)
+        return False
+
+    @property
+    def tuning(self) -> list:
+        """[contiguous-stage points per CTA (0: default), N0 pipelined, N1 pipelined, L2 slab bytes]."""
+        cfg = (ctypes.c_int64 * 4)()
+        _check(load().afft_plan_get_tuning(self._p, cfg), "afft_plan_get_tuning")
+        return [int(v) for v in cfg]
+
+    def set_tuning(self, cfg) -> None:
+        arr = (ctypes.c_int64 * 4)(*[int(v) for v in cfg])
+        _check(load().afft_plan_set_tuning(self._p, arr), "afft_plan_set_tuning")
 
     def describe(self) -> dict:
         import json
@@ -385,6 +411,44 @@ class Multi:
             self.close()
         except Exception:
             pass
+
+
+def tuning_key(shape, kind, precision, batch, gpu_name: str) -> str:
+    """Cache key of a plan's tuned configuration."""
+    kinds = {v: k for k, v in KINDS.items()}
+    precs = {v: k for k, v in PRECISIONS.items()}
+    return "%s/%s/%s/batch%d/%s" % ("x".join(str(int(n)) for n in shape), kinds.get(kind, kind),
+                                    precs.get(precision, precision), int(batch or 1), gpu_name)
+
+
+def tuning_cache_lookup(path: str, key: str):
+    """The stored configuration for `key`, or None (no file, no entry, or a malformed one)."""
+    import json
+    try:
+        with open(path) as fh:
+            cfg = json.load(fh).get(key)
+    except (OSError, ValueError, AttributeError):
+        return None
+    if not isinstance(cfg, list) or len(cfg) != 4 or not all(isinstance(v, int) for v in cfg):
+        return None
+    return cfg
+
+
+def tuning_cache_store(path: str, key: str, cfg) -> None:
+    """Adds or replaces `key` in the cache file (written to a temporary file, then renamed)."""
+    import json
+    try:
+        with open(path) as fh:
+            data = json.load(fh)
+        if not isinstance(data, dict):
+            data = {}
+    except (OSError, ValueError):
+        data = {}
+    data[key] = [int(v) for v in cfg]
+    tmp = "%s.tmp.%d" % (path, os.getpid())
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 def fill_uniform(t: torch.Tensor, seed: int, stream=None) -> torch.Tensor:

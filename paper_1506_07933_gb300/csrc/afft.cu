@@ -1443,6 +1443,31 @@ int afft_plan_tune(afft_plan *p, void *stream)
     return st;
 }
 
+int afft_plan_get_tuning(const afft_plan *p, int64_t cfg[4])
+{
+    if (!p || !cfg) return AFFT_ERR_NULL;
+    cfg[0] = p->contig_target;
+    cfg[1] = p->ax[0].pipe;
+    cfg[2] = p->ax[1].pipe;
+    cfg[3] = (int64_t)p->chunk_bytes;
+    return AFFT_OK;
+}
+
+int afft_plan_set_tuning(afft_plan *p, const int64_t cfg[4])
+{
+    if (!p || !cfg) return AFFT_ERR_NULL;
+    for (int a = 0; a < 2; ++a)
+        if (cfg[1 + a] && !p->ax[a].pipe_avail) return AFFT_ERR_UNSUPPORTED;
+    if (cfg[0] < 0 || cfg[3] < 0) return AFFT_ERR_SIZE;
+    if (!p->four[2].on) {
+        const bool ok = p->precision == AFFT_F64 ? reshape_contig<double2>(p, (int)cfg[0])
+                                                 : reshape_contig<float2>(p, (int)cfg[0]);
+        if (!ok) return AFFT_ERR_UNSUPPORTED;
+    }
+    for (int a = 0; a < 2; ++a) p->ax[a].pipe = cfg[1 + a] != 0;
+    return configure_chunks(p, (size_t)cfg[3]);
+}
+
 int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
 {
     if (!p || !buf) return AFFT_ERR_NULL;

@@ -700,3 +700,26 @@ def test_blocked_layout_eligibility_and_default():
         p.set_blocked(False)
         assert p.describe()["blocked"] == 0
         assert afft.load().afft_plan_workspace_bytes(p._p) == 0
+
+
+def test_tune_with_cache_file(tmp_path):
+    """A tuned configuration is stored under the plan's key and applied, without tuning, to a
+    new plan of the same key; results do not change beyond rounding."""
+    path = str(tmp_path / "tune.json")
+    shape = (64, 64, 128)
+    x = synth.uniform_real(shape, 61).astype(np.float32)
+    with afft.Plan(shape, "r2c", "f32") as p:
+        assert p.tune(cache=path) is False
+        cfg = p.tuning
+        ref = p.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    with afft.Plan(shape, "r2c", "f32") as q:
+        assert q.tune(cache=path) is True
+        assert q.tuning == cfg
+        got = q.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    report("tuned from cache %s" % (shape,), oracle.rel_l2(got, oracle.r2c(x)), TOL["f32"])
+    report("tuned from cache vs tuned", oracle.rel_l2(got, ref), TOL["f32"])
+    with afft.Plan(shape, "r2c", "f32") as r:
+        r.set_tuning([1024, 1, 1, 0])
+        assert r.tuning[0] == 1024
+        with pytest.raises(afft.AfftError):
+            r.set_tuning([-1, 0, 0, 0])
