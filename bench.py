@@ -209,6 +209,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- replicas -----
+# With N > 1 ranks every rank transforms its own field (replicas: the transform does
+# not shard on one node without an all-to-all, and none is built), so the step time
+# is the slowest rank's and the value adds up over ranks.
+
+def max_over_ranks(value, world, dist, device):
+    """The largest of every rank's `value` (world == 1: the value itself)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_percent(step_bytes_per_rank, world, ms, peak):
+    """The metric: every rank's algorithmic bytes per step over the slowest rank's step time,
+    as a percentage of one GPU's measured HBM bandwidth."""
+    return 100.0 * world * step_bytes_per_rank / (ms * 1e-3) / 1e9 / peak
+
+
 # ------------------------------------------------------------------ GPU leg --
 
 def run_gpu(args):
@@ -270,13 +291,10 @@ def run_gpu(args):
     # accuracy of the last timed step (outside the timed region): backward(forward(x)) against x
     xd = x.double()
     round_trip = float(torch.linalg.vector_norm(y.double() - xd) / torch.linalg.vector_norm(xd))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dist, "cuda")
     z, yb, xb = workload_bytes(SHAPE, real_b, cplx_b)
     step_bytes = 2 * (z + yb + xb)
-    value = 100.0 * world * step_bytes / (ms * 1e-3) / 1e9 / peak
+    value = whole_job_percent(step_bytes, world, ms, peak)
 
     # dominant kernel from the per-stage events of the timed region
     fwd = [r for i, r in enumerate(stage) if i % 2 == 0]
@@ -380,15 +398,11 @@ def measure_e2e(args, plan, field, x, X, y, stream, barrier, world, step_bytes, 
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dist, "cuda")
     h2d = plan.input_bytes + plan.output_bytes
     d2h = plan.output_bytes + plan.input_bytes
     plans[1].close()
-    return {"value": 100.0 * world * step_bytes / (e2e_ms * 1e-3) / 1e9 / peak, "unit": UNIT,
+    return {"value": whole_job_percent(step_bytes, world, e2e_ms, peak), "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
             "call": "afft_execute_forward_host + afft_execute_backward_host, two steps in flight on two streams"}
 
