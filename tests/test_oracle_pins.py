@@ -8,6 +8,7 @@ a flipped sign, a transposed axis, a missing 1/N) fails at least one of them;
 ``test_planted_mistakes_are_caught`` shows that on mutated oracles.
 """
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -325,3 +326,54 @@ def test_splitmix64_reference_values():
     states = np.array([(gamma * i) % 2 ** 64 for i in range(3)], dtype=np.uint64)
     out = synth.splitmix64(states)
     assert [int(v) for v in out] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+# --- golden fixture: a 2x4x4 Gaussian-integer DFT (tests/golden/dft_2x4x4.txt) -----------
+
+def _golden_rows():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "dft_2x4x4.txt")
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append(tuple(int(v) for v in line.split()))
+    return rows
+
+
+def _golden_input_ints():
+    return {(j0, j1, j2): ((j0 + 2 * j1 + 3 * j2) % 5 - 2, (j0 * j1 + j2) % 3 - 1)
+            for j0 in range(2) for j1 in range(4) for j2 in range(4)}
+
+
+def _unit_root_pow(m, n):
+    """exp(-2 pi i m / n) for n in {1, 2, 4}, exactly, as a Gaussian integer (re, im)."""
+    q = (m * (4 // n)) % 4            # the same angle in quarter turns
+    return [(1, 0), (0, -1), (-1, 0), (0, 1)][q]
+
+
+def test_golden_2x4x4_fixture_is_the_exact_definition():
+    """Every bin of the fixture equals the 3-D DFT definition evaluated in exact Gaussian-integer
+    arithmetic (no floating point, no oracle code)."""
+    x = _golden_input_ints()
+    rows = _golden_rows()
+    assert len(rows) == 32
+    for k0, k1, k2, re, im in rows:
+        sr = si = 0
+        for (j0, j1, j2), (a, b) in x.items():
+            w = (1, 0)
+            for m, n in ((j0 * k0, 2), (j1 * k1, 4), (j2 * k2, 4)):
+                c, d = _unit_root_pow(m, n)
+                w = (w[0] * c - w[1] * d, w[0] * d + w[1] * c)
+            sr += a * w[0] - b * w[1]
+            si += a * w[1] + b * w[0]
+        assert (sr, si) == (re, im), (k0, k1, k2)
+
+
+@pytest.mark.parametrize("method", ["naive", "fft"])
+def test_oracle_reproduces_golden_2x4x4(method):
+    x = np.zeros((2, 4, 4), dtype=np.complex128)
+    for (j0, j1, j2), (a, b) in _golden_input_ints().items():
+        x[j0, j1, j2] = complex(a, b)
+    X = oracle.c2c(x, -1, method)
+    for k0, k1, k2, re, im in _golden_rows():
+        assert abs(X[k0, k1, k2] - complex(re, im)) < 1e-12
