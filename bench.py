@@ -12,9 +12,18 @@ the 3-pass minimum: one full-array read and write per axis stage.  At N GPUs
 every rank runs its own independent replica (the transform does not shard
 without an all-to-all), and the percentages add up (weak scaling).
 
-`--impl reference` times the FP64 CPU oracle on the host cores instead (the
-only other place this script runs oracle code), on a bounded sample of the
-same workload, reported in the same unit.
+The default line also carries, under "also", the metric's other
+configurations measured in the same run: r2c 512^3 FP64, c2c 512^3 FP32/FP64,
+c2c 1024^3 FP32/FP64/split precision, the fused Poisson solve, the 200-field
+batched uneven workload (solves/s) and the serving workload (solves/s, p50/p99
+at 200 and 700 requests/s and at saturation), plus cuFFT on the same shapes as
+a reference baseline.  `--no-extra` leaves them out.
+
+`cpu_baseline` times the CPU oracle on the host cores on the same 512^3 field:
+the FP32 build of its source for this FP32 workload (the FP64 build and
+single-threaded numpy.fft beside it).  `--impl reference` times that FP32
+oracle build alone, one whole 512^3 r2c + c2r per step (the only other place
+this script runs oracle code), reported in the same unit.
 """
 from __future__ import annotations
 
@@ -39,8 +48,6 @@ WORKLOAD = ("r2c forward + c2r backward, 512x512x512 %s random-mode field (64 mo
             "+1e-3 noise)")
 STAGE_NAMES_FWD = ["r2c z-stage (N2)", "strided y-stage (N1)", "strided x-stage (N0)"]
 STAGE_NAMES_BWD = ["strided x-stage (N0)", "strided y-stage (N1)", "c2r z-stage (N2)"]
-KERNEL_NAMES_FWD = ["k_r2c", "k_strided_pipe", "k_strided_pipe"]
-KERNEL_NAMES_BWD = ["k_strided_pipe", "k_strided_pipe", "k_c2r"]
 
 
 def peaks():
@@ -152,61 +159,88 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU leg --
 
-def cpu_oracle_sample(min_seconds=10.0, shape=(128, 128, 128)):
-    """Times the FP64 oracle (r2c + c2r, all host cores) on a smaller cube of the same kind.
+def cpu_field(shape=SHAPE):
+    """The benchmark's FP32 random-mode field (mode seed 5121), as the GPU arm's rank 0 uses."""
+    import numpy as np
+    from paper_1506_07933_gb300 import synth
+    return synth.random_mode_field(shape, 5121, n_modes=64, noise=1e-3).astype(np.float32)
 
-    Returns (seconds per sample step, bytes per sample step, threads, description)."""
+
+def cpu_step_seconds(field, engine, threads=None):
+    """Seconds of one r2c + c2r of `field` on the CPU: engine "oracle_f32" (the oracle's source
+    built with FP32 arithmetic, all threads), "oracle_f64" (the FP64 oracle) or "numpy"
+    (numpy.fft.rfftn / irfftn, pocketfft, one thread)."""
     import numpy as np
     import oracle
-    from paper_1506_07933_gb300 import synth
+    n2 = field.shape[2]
+    t0 = time.perf_counter()
+    if engine == "oracle_f32":
+        oracle.c2r_f32(oracle.r2c_f32(field, threads), n2, threads)
+    elif engine == "oracle_f64":
+        oracle.c2r(oracle.r2c(field, "fft", threads), n2, "fft", threads)
+    else:
+        np.fft.irfftn(np.fft.rfftn(field, axes=(0, 1, 2)), s=field.shape, axes=(0, 1, 2))
+    return time.perf_counter() - t0
 
-    x = synth.random_mode_field(shape, 5121, n_modes=64, noise=1e-3)
+
+def cpu_baseline_block(step_bytes, peak):
+    """The CPU baseline of the GPU arm: the oracle timed on the host cores on the same 512^3
+    field (the FP32 build: one untimed and one timed step), with the FP64 oracle and
+    single-threaded numpy.fft timed once each beside it."""
+    import oracle
+    field = cpu_field()
     threads = oracle.max_threads()
-    oracle.c2r(oracle.r2c(x), shape[2])  # warm up
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        X = oracle.r2c(x, "fft", threads)
-        oracle.c2r(X, shape[2], "fft", threads)
-        reps += 1
-        if time.perf_counter() - t0 >= min_seconds:
-            break
-    dt = (time.perf_counter() - t0) / reps
-    z, y, xx = workload_bytes(shape, 8, 16)
-    desc = ("oracle r2c+c2r (recursive mixed-radix, FP64) of a %dx%dx%d random-mode field, %d rep(s), "
-            "%d threads; extrapolated to the 512^3 step by algorithmic bytes" % (shape + (reps, threads)))
-    return dt, 2 * (z + y + xx), threads, desc
+    cpu_step_seconds(field, "oracle_f32", threads)
+    t32 = cpu_step_seconds(field, "oracle_f32", threads)
+    t64 = cpu_step_seconds(field, "oracle_f64", threads)
+    tnp = cpu_step_seconds(field, "numpy")
+    pct = lambda t: 100.0 * step_bytes / t / 1e9 / peak
+    return {"value": pct(t32), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "one whole r2c + c2r of the same 512^3 float32 field per step, the oracle's "
+                      "recursive mixed-radix source built with FP32 arithmetic, %d threads (1 untimed + "
+                      "1 timed step)" % threads,
+            "ms_per_step": t32 * 1e3,
+            "oracle_fp64": {"value": pct(t64), "ms_per_step": t64 * 1e3, "cores": threads},
+            "numpy_fft_single_thread": {"value": pct(tnp), "ms_per_step": tnp * 1e3, "cores": 1}}
 
 
 def run_reference(args):
+    """The reference arm: the oracle (FP32 build of its source) on the host cores, one whole
+    r2c + c2r of the 512^3 float32 field per step; rank 0 alone under torchrun."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle
+    oracle.build()
     peak, _ = peaks()
-    sample = (128, 128, 128)
-    times = []
-    per_step_bytes = None
-    for i in range(args.warmup + args.steps):
-        dt, b, threads, desc = cpu_oracle_sample(min_seconds=0.0, shape=sample)
-        per_step_bytes = b
-        if i >= args.warmup:
-            times.append(dt)
-    t = statistics.median(times)
-    value = 100.0 * per_step_bytes / t / 1e9 / peak
-    full_bytes = 2 * sum(workload_bytes(SHAPE, 4, 8))
-    t_full = t * full_bytes / per_step_bytes   # the 512^3 step at the sample's byte rate
+    field = cpu_field()
+    threads = oracle.max_threads()
+    for _ in range(args.warmup):
+        cpu_step_seconds(field, "oracle_f32", threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_step_seconds(field, "oracle_f32", threads)
+    t = (time.perf_counter() - t0) / args.steps
+    step_bytes = 2 * sum(workload_bytes(SHAPE, 4, 8))
+    value = 100.0 * step_bytes / t / 1e9 / peak
+    sample = ("one whole r2c + c2r of the 512^3 float32 field per step, the oracle's recursive "
+              "mixed-radix source built with FP32 arithmetic, %d threads" % threads)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "sample_ms_per_step": t * 1e3,
-        "config": {"workload": WORKLOAD % "float32",
-                   "sample": "FP64 CPU oracle on a %dx%dx%d field of the same kind per step, scaled to the "
-                             "512^3 step by algorithmic bytes" % sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "r2c+c2r of a %dx%dx%d field per step" % sample},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": gpu_config(step_bytes, 1, (SHAPE[0] * SHAPE[1] * SHAPE[2] * 4) >> 20),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def gpu_config(step_bytes, world, input_mb):
+    """The line's `config`, the same for both arms."""
+    return {"workload": WORKLOAD % "float32",
+            "l2": "inputs larger than L2 (%d MB > 129 MB), no flush" % input_mb,
+            "bytes_per_step": step_bytes, "parallelism": "replicas x%d" % world}
 
 
 # ------------------------------------------------------------- replicas -----
@@ -299,9 +333,10 @@ def run_gpu(args):
     # dominant kernel from the per-stage events of the timed region
     fwd = [r for i, r in enumerate(stage) if i % 2 == 0]
     bwd = [r for i, r in enumerate(stage) if i % 2 == 1]
+    desc = plan.describe()
     kernels = []
-    for rows, names, knames, sbytes in ((fwd, STAGE_NAMES_FWD, KERNEL_NAMES_FWD, (z, yb, xb)),
-                                        (bwd, STAGE_NAMES_BWD, KERNEL_NAMES_BWD, (xb, yb, z))):
+    for rows, names, knames, sbytes in ((fwd, STAGE_NAMES_FWD, desc["stage_kernels_forward"], (z, yb, xb)),
+                                        (bwd, STAGE_NAMES_BWD, desc["stage_kernels_backward"], (xb, yb, z))):
         for s in range(3):
             ts = [r[s] for r in rows]
             kernels.append({"stage": names[s] + (" fwd" if rows is fwd else " bwd"), "kernel": knames[s],
@@ -324,9 +359,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": prec, "data": "synthetic",
-        "config": {"workload": WORKLOAD % {"f32": "float32", "f64": "float64"}[prec],
-                   "l2": "inputs larger than L2 (%d MB > 129 MB), no flush" % (plan.input_bytes >> 20),
-                   "bytes_per_step": step_bytes, "parallelism": "replicas x%d" % world},
+        "config": gpu_config(step_bytes, world, plan.input_bytes >> 20),
         "roofline": roofline,
         "stages": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in kk.items()} for kk in kernels],
         "stage_ms_total": total_stage_ms,
@@ -341,16 +374,15 @@ def run_gpu(args):
     plan.close()
     torch.cuda.empty_cache()
 
-    if args.extra and rank == 0:
-        line["also"] = extra_configs(afft, torch, peak)
-        line["cufft"] = cufft_reference(torch, peak)
-        line["batched"] = batched_workload(afft, torch)
-        line["serving"] = serving_workload(torch)
+    if not args.no_extra and rank == 0:
+        t_extra = time.time()
+        line["also"] = {"roofline_configs": extra_configs(afft, torch, peak),
+                        "batched": batched_workload(afft, torch),
+                        "serving": serving_workload(torch),
+                        "cufft_reference": cufft_reference(torch, peak)}
+        line["also"]["seconds"] = round(time.time() - t_extra, 1)
     if rank == 0 and world == 1 and not args.no_cpu:
-        dt, b, threads, desc = cpu_oracle_sample(min_seconds=args.cpu_seconds)
-        line["cpu_baseline"] = {"value": 100.0 * b / dt / 1e9 / peak, "unit": UNIT, "cores": threads,
-                                "kind": "oracle", "sample": desc,
-                                "ms_per_step_extrapolated": dt * 1e3 * step_bytes / b}
+        line["cpu_baseline"] = cpu_baseline_block(step_bytes, peak)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -408,24 +440,10 @@ def measure_e2e(args, plan, field, x, X, y, stream, barrier, world, step_bytes, 
 
 
 def mode_field_gpu(torch, n, seed, n_modes=64, noise=1e-3):
-    """The random-mode field of synth.random_mode_field (same modes, same recipe) evaluated on the
-    GPU with torch: a rank-n_modes sum of outer products of 1-D exponentials, plus noise from a
-    seeded torch generator.  Input generation only; none of the transform's arithmetic."""
-    import numpy as np
+    """The random-mode field (synth.random_mode_field_torch: same modes and recipe) of an n^3 grid,
+    evaluated on the GPU and rounded to float32.  Input generation only."""
     from paper_1506_07933_gb300 import synth
-    ks, amp, phase = synth.draw_modes((n, n, n), n_modes, seed)
-    j = torch.arange(n, device="cuda", dtype=torch.int64)
-    def exps(d):
-        k = torch.tensor(ks[:, d], device="cuda", dtype=torch.int64)
-        ph = torch.remainder(k[:, None] * j[None, :], n).to(torch.float64)
-        return torch.exp(2j * torch.pi * ph / n)
-    e0, e1, e2 = exps(0), exps(1), exps(2)
-    c = torch.tensor(amp * np.exp(1j * phase), device="cuda")
-    f = torch.einsum("m,mi,mj,mk->ijk", c, e0, e1, e2).real
-    g = torch.Generator(device="cuda")
-    g.manual_seed(seed + 1)
-    f += noise * torch.randn(f.shape, device="cuda", dtype=torch.float64, generator=g)
-    return f.to(torch.float32)
+    return synth.random_mode_field_torch((n, n, n), seed, n_modes, noise).to(torch.float32)
 
 
 def batched_workload(afft, torch, steps=10, warmup=3, count=200, seed=200):
@@ -643,9 +661,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["afft", "reference"], default="afft")
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
-    ap.add_argument("--extra", action="store_true", help="also time the other roofline configurations")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave out the metric's other configurations (the 'also' block)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -91,8 +91,12 @@ enum {
  * library takes an N0 x N1 x N2 array).  Factors each axis into radix
  * 16/8/4/2/3/5 passes (the Cooley-Tukey reduction of Section 2), computes
  * the twiddle tables in FP64 on the current device, and allocates the
- * workspace.  Each n[i] must be >= 1 with prime factors in {2, 3, 5}, and
- * at most 4096 (longer lines return AFFT_ERR_UNSUPPORTED).
+ * workspace.  Each n[i] must be >= 1 with prime factors in {2, 3, 5}.  A line
+ * longer than 4096 points (the longest one CTA transforms) is split four-step,
+ * n = n_a n_b with both factors at most 4096, through a plan-owned buffer of
+ * the array's size; AFFT_ERR_UNSUPPORTED when no such split exists (n above
+ * 4096^2), and for an r2c plan whose contiguous half length n[2]/2 exceeds 4096
+ * (that axis is not split).
  *   out:       receives the plan (set to NULL on failure).
  *   n:         host array of 3 sizes, slowest first.
  *   kind:      AFFT_C2C or AFFT_R2C.
@@ -340,7 +344,10 @@ int afft_fill_uniform(void *dev_out, int64_t count, uint64_t seed, int precision
  *   stream:    a cudaStream_t (NULL = legacy default stream); asynchronous.
  * Errors as afft_plan_create / afft_execute_backward, plus AFFT_ERR_SCRATCH when
  * n0*n1*(n2/2+1) complex values exceed the array's 63.5 MiB workspace part
- * (e.g. 256^3 float32 does not fit; 128^3 float64 does).
+ * (e.g. 256^3 float32 does not fit; 128^3 float64 does), and
+ * AFFT_ERR_UNSUPPORTED when n[0], n[1] or n[2]/2 exceeds 4096 (such lines need
+ * the four-step split's buffer, which this entry point does not have; e.g.
+ * (1, 1, 16384) is refused although it fits the array) or for AFFT_F32_SPLIT.
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it: make that first call before any
  * stream capture.  All calls share the array and leave their data in it:

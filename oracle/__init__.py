@@ -31,18 +31,22 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB32 = os.path.join(_HERE, "liboracle_f32.so")
 _lib = None
+_lib32 = None
 
 METHODS = {"naive": 0, "fft": 1}
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so with gcc (OpenMP on)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    """Compile oracle.c into liboracle.so with gcc (OpenMP on), and the same source with
+    -DORC_REAL=float into liboracle_f32.so (the FP32 CPU baseline; never a parity reference)."""
+    for lib, extra in ((_LIB, []), (_LIB32, ["-DORC_REAL=float"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+            tmp = lib + ".tmp.%d" % os.getpid()
+            subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall", *extra,
+                                   "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, lib)
     return _LIB
 
 
@@ -62,6 +66,41 @@ def _load():
         lib.orc_max_threads.restype = c_int
         _lib = lib
     return _lib
+
+
+def _load32():
+    """The FP32 build: the same entry points on float data."""
+    global _lib32
+    if _lib32 is None:
+        build()
+        lib = ctypes.CDLL(_LIB32)
+        i64, dp, c_int = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+        lib.orc_r2c_3d.argtypes = [dp, dp, i64, i64, i64, c_int, c_int]
+        lib.orc_c2r_3d.argtypes = [dp, dp, i64, i64, i64, c_int, c_int]
+        lib.orc_r2c_3d.restype = lib.orc_c2r_3d.restype = c_int
+        _lib32 = lib
+    return _lib32
+
+
+def r2c_f32(x, nthreads=None) -> np.ndarray:
+    """r2c by the FP32 build of the same source (recursive mixed-radix engine): the CPU baseline
+    of FP32 transforms.  float32 [n0, n1, n2] -> complex64 [n0, n1, n2//2 + 1]."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n0, n1, n2 = x.shape
+    out = np.empty((n0, n1, n2 // 2 + 1), dtype=np.complex64)
+    _check(_load32().orc_r2c_3d(x.ctypes.data, out.ctypes.data, n0, n1, n2, METHODS["fft"], _threads(nthreads)))
+    return out
+
+
+def c2r_f32(X, n2: int, nthreads=None) -> np.ndarray:
+    """c2r by the FP32 build (x 1/N): complex64 [n0, n1, n2//2 + 1] -> float32 [n0, n1, n2]."""
+    X = np.ascontiguousarray(X, dtype=np.complex64)
+    n0, n1, nh = X.shape
+    if nh != n2 // 2 + 1:
+        raise ValueError("half-spectrum width must be n2//2 + 1")
+    out = np.empty((n0, n1, n2), dtype=np.float32)
+    _check(_load32().orc_c2r_3d(X.ctypes.data, out.ctypes.data, n0, n1, n2, METHODS["fft"], _threads(nthreads)))
+    return out
 
 
 def max_threads() -> int:

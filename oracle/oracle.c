@@ -29,7 +29,8 @@
  *            (radices 2, 3, 5; any other prime factor falls back to the naive
  *            sum), in double, with unit roots from the same long-double table.
  *
- * Complex data is interleaved (re, im) double, row-major [n0][n1][n2] with n2
+ * Complex data is interleaved (re, im) real_t (double unless built with
+ * -DORC_REAL=float), row-major [n0][n1][n2] with n2
  * contiguous.  Half-spectrum (r2c) arrays are [n0][n1][n2/2+1].
  *
  * Pins (tests/test_oracle_pins.py): impulse, shift theorem, plane waves, real
@@ -45,7 +46,14 @@
 #include <omp.h>
 #endif
 
-typedef struct { double re, im; } cplx;
+/* The arithmetic type: double (the oracle).  The same source compiled with
+ * -DORC_REAL=float is the FP32 build that the benchmark times as the CPU
+ * baseline of FP32 transforms; it is never used as a parity reference. */
+#ifndef ORC_REAL
+#define ORC_REAL double
+#endif
+typedef ORC_REAL real_t;
+typedef struct { real_t re, im; } cplx;
 
 #define ORC_OK 0
 #define ORC_ERR_ARG 1
@@ -77,8 +85,8 @@ static void dft_line_naive(const cplx *x, cplx *X, int64_t n,
             sr += xr * wr[m] - xi * wi[m];
             si += xr * wi[m] + xi * wr[m];
         }
-        X[k].re = (double)sr;
-        X[k].im = (double)si;
+        X[k].re = (real_t)sr;
+        X[k].im = (real_t)si;
     }
 }
 
@@ -111,7 +119,7 @@ static void fft_rec(const cplx *x, int64_t stride, cplx *X, int64_t n,
     if (p == n) {
         /* prime length without a small factor: the definition itself */
         for (int64_t k = 0; k < n; ++k) {
-            double sr = 0.0, si = 0.0;
+            real_t sr = 0.0, si = 0.0;
             for (int64_t j = 0; j < n; ++j) {
                 const cplx w = wroot[((j * k) % n) * step];
                 const cplx v = x[j * stride];
@@ -130,7 +138,7 @@ static void fft_rec(const cplx *x, int64_t stride, cplx *X, int64_t n,
     for (int64_t k = 0; k < m; ++k) {
         for (int64_t q = 0; q < p; ++q) t[q] = X[q * m + k];
         for (int64_t s = 0; s < p; ++s) {
-            double sr = 0.0, si = 0.0;
+            real_t sr = 0.0, si = 0.0;
             for (int64_t q = 0; q < p; ++q) {
                 int64_t e = (q * (k + m * s)) % n;
                 const cplx w = wroot[e * step];
@@ -150,7 +158,7 @@ static void fft_rec(const cplx *x, int64_t stride, cplx *X, int64_t n,
  * [outer][n][inner] (the axis has length n and element stride `inner`).
  * sign = -1 forward, +1 backward (unscaled).  method 0 naive, 1 fft.
  */
-int orc_dft_axis(double *data, int64_t outer, int64_t n, int64_t inner,
+int orc_dft_axis(real_t *data, int64_t outer, int64_t n, int64_t inner,
                  int sign, int method, int nthreads)
 {
     if (!data || outer < 0 || n < 1 || inner < 0 || (sign != 1 && sign != -1) ||
@@ -164,7 +172,7 @@ int orc_dft_axis(double *data, int64_t outer, int64_t n, int64_t inner,
     cplx *wd = (cplx *)malloc(sizeof(cplx) * (size_t)n);
     if (!wr || !wi || !wd) { free(wr); free(wi); free(wd); return ORC_ERR_NOMEM; }
     unit_roots_ld(n, sign, wr, wi);
-    for (int64_t m = 0; m < n; ++m) { wd[m].re = (double)wr[m]; wd[m].im = (double)wi[m]; }
+    for (int64_t m = 0; m < n; ++m) { wd[m].re = (real_t)wr[m]; wd[m].im = (real_t)wi[m]; }
 
     const int64_t lines = outer * inner;
     int status = ORC_OK;
@@ -210,7 +218,7 @@ static int bad_dims(int64_t n0, int64_t n1, int64_t n2)
  * direction +1: backward, axes 0,1,2 (Algorithm 1 right), then x 1/N
  * (Section 2, footnote 2).  in and out may alias.
  */
-int orc_c2c_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2,
+int orc_c2c_3d(const real_t *in, real_t *out, int64_t n0, int64_t n1, int64_t n2,
                int direction, int method, int nthreads)
 {
     if (!in || !out || bad_dims(n0, n1, n2) || (direction != 1 && direction != -1))
@@ -226,7 +234,7 @@ int orc_c2c_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2
         if ((s = orc_dft_axis(out, 1, n0, n1 * n2, 1, method, nthreads))) return s;
         if ((s = orc_dft_axis(out, n0, n1, n2, 1, method, nthreads))) return s;
         if ((s = orc_dft_axis(out, n0 * n1, n2, 1, 1, method, nthreads))) return s;
-        const double inv = 1.0 / (double)N;
+        const real_t inv = 1.0 / (real_t)N;
         for (int64_t i = 0; i < 2 * N; ++i) out[i] *= inv;
     }
     return ORC_OK;
@@ -240,7 +248,7 @@ int orc_c2c_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2
  * since the transforms along axes 0 and 1 act on each k2 column separately.
  * in: n0*n1*n2 doubles.  out: n0*n1*(n2/2+1) interleaved complex.
  */
-int orc_r2c_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2,
+int orc_r2c_3d(const real_t *in, real_t *out, int64_t n0, int64_t n1, int64_t n2,
                int method, int nthreads)
 {
     if (!in || !out || bad_dims(n0, n1, n2)) return ORC_ERR_ARG;
@@ -248,7 +256,7 @@ int orc_r2c_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2
     cplx *full = (cplx *)malloc(sizeof(cplx) * (size_t)(n0 * n1 * n2));
     if (!full) return ORC_ERR_NOMEM;
     for (int64_t i = 0; i < n0 * n1 * n2; ++i) { full[i].re = in[i]; full[i].im = 0.0; }
-    int s = orc_dft_axis((double *)full, n0 * n1, n2, 1, -1, method, nthreads);
+    int s = orc_dft_axis((real_t *)full, n0 * n1, n2, 1, -1, method, nthreads);
     if (s) { free(full); return s; }
     cplx *h = (cplx *)out;
     for (int64_t l = 0; l < n0 * n1; ++l)
@@ -266,7 +274,7 @@ int orc_r2c_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2
  * its real part kept; finally x 1/N.  `in` is not modified.
  * in: n0*n1*(n2/2+1) interleaved complex.  out: n0*n1*n2 doubles.
  */
-int orc_c2r_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2,
+int orc_c2r_3d(const real_t *in, real_t *out, int64_t n0, int64_t n1, int64_t n2,
                int method, int nthreads)
 {
     if (!in || !out || bad_dims(n0, n1, n2)) return ORC_ERR_ARG;
@@ -277,8 +285,8 @@ int orc_c2r_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2
     if (!h || !full) { free(h); free(full); return ORC_ERR_NOMEM; }
     memcpy(h, in, sizeof(cplx) * (size_t)(lines * nh));
     int s;
-    if ((s = orc_dft_axis((double *)h, 1, n0, n1 * nh, 1, method, nthreads)) ||
-        (s = orc_dft_axis((double *)h, n0, n1, nh, 1, method, nthreads))) {
+    if ((s = orc_dft_axis((real_t *)h, 1, n0, n1 * nh, 1, method, nthreads)) ||
+        (s = orc_dft_axis((real_t *)h, n0, n1, nh, 1, method, nthreads))) {
         free(h); free(full); return s;
     }
     for (int64_t l = 0; l < lines; ++l) {
@@ -296,9 +304,9 @@ int orc_c2r_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2
         }
     }
     free(h);
-    s = orc_dft_axis((double *)full, lines, n2, 1, 1, method, nthreads);
+    s = orc_dft_axis((real_t *)full, lines, n2, 1, 1, method, nthreads);
     if (s) { free(full); return s; }
-    const double inv = 1.0 / (double)(n0 * n1 * n2);
+    const real_t inv = 1.0 / (real_t)(n0 * n1 * n2);
     for (int64_t i = 0; i < lines * n2; ++i) out[i] = full[i].re * inv;
     free(full);
     return ORC_OK;
@@ -312,8 +320,8 @@ int orc_c2r_3d(const double *in, double *out, int64_t n0, int64_t n1, int64_t n2
  * integer phase (j k) mod n).  in: complex (is_real = 0) or real (is_real = 1)
  * [n0][n1][n2]; ks: nk triples (k0, k1, k2) with 0 <= ki < ni; out: nk complex.
  */
-int orc_dft_bins(const double *in, int is_real, int64_t n0, int64_t n1, int64_t n2,
-                 const int64_t *ks, int64_t nk, double *out, int nthreads)
+int orc_dft_bins(const real_t *in, int is_real, int64_t n0, int64_t n1, int64_t n2,
+                 const int64_t *ks, int64_t nk, real_t *out, int nthreads)
 {
     if (!in || !ks || !out || bad_dims(n0, n1, n2) || nk < 0) return ORC_ERR_ARG;
     for (int64_t b = 0; b < nk; ++b)
@@ -328,28 +336,28 @@ int orc_dft_bins(const double *in, int is_real, int64_t n0, int64_t n1, int64_t 
         if (!w0 || !w1 || !w2) { free(w0); free(w1); free(w2); return ORC_ERR_NOMEM; }
         for (int64_t j = 0; j < n0; ++j) {
             long double a = ORC_TWO_PI * (long double)((j * k0) % n0) / (long double)n0;
-            w0[j].re = (double)cosl(a); w0[j].im = -(double)sinl(a);
+            w0[j].re = (real_t)cosl(a); w0[j].im = -(real_t)sinl(a);
         }
         for (int64_t j = 0; j < n1; ++j) {
             long double a = ORC_TWO_PI * (long double)((j * k1) % n1) / (long double)n1;
-            w1[j].re = (double)cosl(a); w1[j].im = -(double)sinl(a);
+            w1[j].re = (real_t)cosl(a); w1[j].im = -(real_t)sinl(a);
         }
         for (int64_t j = 0; j < n2; ++j) {
             long double a = ORC_TWO_PI * (long double)((j * k2) % n2) / (long double)n2;
-            w2[j].re = (double)cosl(a); w2[j].im = -(double)sinl(a);
+            w2[j].re = (real_t)cosl(a); w2[j].im = -(real_t)sinl(a);
         }
-        double sr = 0.0, si = 0.0;
+        real_t sr = 0.0, si = 0.0;
 #ifdef _OPENMP
         if (nthreads < 1) nthreads = 1;
 #pragma omp parallel for num_threads(nthreads) reduction(+ : sr, si) schedule(static)
 #endif
         for (int64_t j0 = 0; j0 < n0; ++j0) {
-            double ar = 0.0, ai = 0.0;
+            real_t ar = 0.0, ai = 0.0;
             for (int64_t j1 = 0; j1 < n1; ++j1) {
-                double br = 0.0, bi = 0.0;
+                real_t br = 0.0, bi = 0.0;
                 const int64_t base = (j0 * n1 + j1) * n2;
                 if (is_real) {
-                    const double *x = in + base;
+                    const real_t *x = in + base;
                     for (int64_t j2 = 0; j2 < n2; ++j2) {
                         br += x[j2] * w2[j2].re;
                         bi += x[j2] * w2[j2].im;

@@ -1468,6 +1468,21 @@ int afft_plan_set_tuning(afft_plan *p, const int64_t cfg[4])
     return configure_chunks(p, (size_t)cfg[3]);
 }
 
+namespace {
+
+// Name of the kernel a strided stage of axis a launches over rows of W complex values.
+const char *strided_kernel_name(const afft_plan *p, int a, long long W)
+{
+    const AxisPlan &ap = p->ax[a];
+    if (!ap.pipe) return "k_strided";
+    if (cplx_size(p->precision) == 8 && (W % 2) == 1 && ap.rp_slots > 0 && ap.desc.n % 2 == 0 &&
+        ap.desc.n / 2 <= 256 && 2 * W >= ap.ks->pipe_lines + 2)
+        return "k_strided_pipe_rp";
+    return "k_strided_pipe";
+}
+
+}  // namespace
+
 int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
 {
     if (!p || !buf) return AFFT_ERR_NULL;
@@ -1478,19 +1493,29 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         radix[a][0] = 0;
         for (int i = 0; i < d.npass && o < 56; ++i) o += snprintf(radix[a] + o, 64 - o, i ? "x%d" : "%d", d.radix[i]);
     }
+    // kernels of the stages in launch order (forward N2, N1, N0; backward N0, N1, N2); a four-step
+    // axis adds k_fourstep after its strided half
+    const bool blk = use_blocked(p);
+    const long long W1 = p->nh, W0 = p->n[1] * p->nh;
+    const char *zf = p->four[2].on ? "k_strided+k_fourstep" : p->kind == AFFT_R2C ? "k_r2c" : "k_contig";
+    const char *zb = p->four[2].on ? "k_strided+k_fourstep" : p->kind == AFFT_R2C ? "k_c2r" : "k_contig";
+    const char *y = blk ? "k_strided_pipe" : p->four[1].on ? "k_strided+k_fourstep" : strided_kernel_name(p, 1, W1);
+    const char *x = blk ? "k_strided_pipe" : p->four[0].on ? "k_strided+k_fourstep" : strided_kernel_name(p, 0, W0);
     const int need = snprintf(
         buf, len,
         "{\"n\": [%lld, %lld, %lld], \"batch\": %lld, \"kind\": \"%s\", \"precision\": \"%s\", "
         "\"radix\": [\"%s\", \"%s\", \"%s\"], \"specialised\": [%d, %d, %d], \"four_step\": [%d, %d, %d], "
         "\"pipelined\": [%d, %d], \"contig_lines\": %d, \"strided_lines\": [%d, %d], "
-        "\"l2_slab_planes\": %d, \"blocked\": %d}",
+        "\"l2_slab_planes\": %d, \"blocked\": %d, "
+        "\"stage_kernels_forward\": [\"%s\", \"%s\", \"%s\"], \"stage_kernels_backward\": [\"%s\", \"%s\", \"%s\"]}",
         (long long)p->n[0], (long long)p->n[1], (long long)p->n[2], (long long)p->batch,
         p->kind == AFFT_C2C ? "c2c" : "r2c",
         p->precision == AFFT_F64 ? "f64" : p->precision == AFFT_F32_SPLIT ? "f32split" : "f32", radix[0], radix[1], radix[2],
         !p->ax[0].ks->generic, !p->ax[1].ks->generic, !p->ax[2].ks->generic, p->four[0].on, p->four[1].on,
         p->four[2].on, p->ax[0].pipe, p->ax[1].pipe, p->ax[2].launch.lines,
         p->ax[0].pipe ? p->ax[0].ks->pipe_lines : p->ax[0].launch.lines,
-        p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, p->chunk_planes, (int)use_blocked(p));
+        p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, p->chunk_planes, (int)blk,
+        blk ? "k_contig" : zf, y, x, x, y, blk ? "k_contig" : zb);
     if (need < 0) return AFFT_ERR_CUDA;
     return (size_t)need < len ? AFFT_OK : AFFT_ERR_SIZE;
 }

@@ -155,12 +155,16 @@ bool shape_strided(Axis &a, long long outer, long long W, size_t elem, size_t ma
     }
 }
 
-bool shape_contig(Axis &a, long long nlines, size_t elem, size_t max_smem)
+// even_lines: an even line count where possible, so that every CTA's run of complex64 lines
+// of an odd bin count starts 16-byte aligned (the c2r kernel then stages it with 16-byte
+// copies), as plans do.
+bool shape_contig(Axis &a, long long nlines, size_t elem, size_t max_smem, bool even_lines)
 {
     const int target = elem == 8 ? 4096 : 2048;
     int lines = target / (a.d.n > 0 ? a.d.n : 1);
     if (lines < 1) lines = 1;
     if (lines > nlines) lines = (int)(nlines > 0 ? nlines : 1);
+    if (even_lines && lines > 1 && (lines & 1)) --lines;
     const int row = (int)(128 / elem);
     for (;;) {
         const int thr = threads_for(a.d, lines);
@@ -250,7 +254,7 @@ int run(const int64_t n[3], int precision, const void *in, void *out, cudaStream
     };
     if (!shape_strided(ax[0], 1, n1 * nh, elem, budget(ax[0])) ||
         !shape_strided(ax[1], n0, nh, elem, budget(ax[1])) ||
-        !shape_contig(ax[2], n0 * n1, elem, budget(ax[2])))
+        !shape_contig(ax[2], n0 * n1, elem, budget(ax[2]), elem == 8 && (nh & 1)))
         return AFFT_ERR_UNSUPPORTED;
     if (cudaFuncSetAttribute(ax[0].ks->fn[KS_STRIDED_BWD], cudaFuncAttributeMaxDynamicSharedMemorySize,
                              max_smem) != cudaSuccess ||

@@ -13,6 +13,8 @@ Experiments"); the recipes below fix what those arrays contain.
   a_m ~ N(0, 1), phi_m ~ U[0, 2 pi), plus optional 1e-3 N(0, 1) noise.
   The field is evaluated as a rank-M sum of outer products of 1-D complex
   exponentials (a matrix product), never through a Fourier transform.
+* ``plane_wave_sum_torch`` / ``random_mode_field_torch``: the same kind of
+  fields evaluated with torch on the GPU, for sizes too large for the host.
 * ``splitmix64_uniform``: the counter-based generator used for inputs too
   large to draw on the host.  value(i, part) =
   (splitmix64(seed ^ (2 i + part)) >> 40) * 2**-24 * 2 - 1, with splitmix64
@@ -89,6 +91,40 @@ def random_mode_field(shape, seed: int, n_modes: int = 64, noise: float = 1e-3,
     f = f.astype(dtype)
     if return_modes:
         return f, (ks, amp, phase)
+    return f
+
+
+def plane_wave_sum_torch(shape, ks, coef, device="cuda"):
+    """sum_m coef_m exp(+i k_m . x) on x_j = 2 pi j / n as a complex128 torch tensor on `device`:
+    a rank-M sum of outer products of 1-D exponentials (exact-integer phases k j mod n), never a
+    Fourier transform.  For inputs too large to build on the host; torch is imported here only."""
+    import torch
+    n0, n1, n2 = (int(s) for s in shape)
+    ks = np.asarray(ks, dtype=np.int64).reshape(-1, 3)
+
+    def exps(d, n):
+        j = torch.arange(n, device=device, dtype=torch.int64)
+        k = torch.tensor(ks[:, d], device=device, dtype=torch.int64)
+        ph = torch.remainder(k[:, None] * j[None, :], n).to(torch.float64)
+        return torch.exp(2j * torch.pi * ph / n)
+
+    e0, e1, e2 = exps(0, n0), exps(1, n1), exps(2, n2)
+    c = torch.tensor(np.asarray(coef, dtype=np.complex128), device=device)
+    a = (c[:, None, None] * e0[:, :, None] * e1[:, None, :]).reshape(len(c), n0 * n1)
+    return (a.T @ e2).reshape(n0, n1, n2)
+
+
+def random_mode_field_torch(shape, seed: int, n_modes: int = 64, noise: float = 1e-3, device="cuda"):
+    """random_mode_field (same modes) evaluated with torch on `device` in float64; the noise comes
+    from a torch generator seeded with seed + 1 (so it differs from the numpy recipe's noise)."""
+    import torch
+    shape = tuple(int(s) for s in shape)
+    ks, amp, phase = draw_modes(shape, n_modes, seed)
+    f = plane_wave_sum_torch(shape, ks, amp * np.exp(1j * phase), device).real.contiguous()
+    if noise:
+        g = torch.Generator(device=device)
+        g.manual_seed(seed + 1)
+        f += noise * torch.randn(f.shape, device=device, dtype=torch.float64, generator=g)
     return f
 
 

@@ -132,3 +132,17 @@ def test_tuning_cache_file(tmp_path):
     assert afft.tuning_cache_lookup(path, k1) is None
     afft.tuning_cache_store(path, k1, [4096, 1, 1, 0])
     assert afft.tuning_cache_lookup(path, k1) == [4096, 1, 1, 0]
+
+
+def test_noalloc_source_calls_no_allocator():
+    """The no-allocation entry point's translation unit names no allocating CUDA call in its code
+    (comments aside), so a later edit that adds one fails here before it reaches a GPU."""
+    path = os.path.join(os.path.dirname(libbuild.__file__), "csrc", "noalloc.cu")
+    src = open(path).read()
+    code = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    code = re.sub(r"//[^\n]*", "", code)
+    for name in ("cudaMalloc", "cudaMallocAsync", "cudaMallocManaged", "cudaMallocHost", "cudaHostAlloc",
+                 "cudaFree", "cudaFreeAsync", "cudaMallocPitch", "cudaMalloc3D", "cuMemAlloc", "cuMemCreate",
+                 "malloc(", "new "):
+        assert name not in code, name
+    assert "cudaGetSymbolAddress" in code

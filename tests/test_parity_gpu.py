@@ -250,6 +250,88 @@ def test_r2c_512cubed_full_size(prec):
     report("r2c 512^3 %s sampled bins (%d)" % (prec, len(ks)), oracle.rel_l2(got, ref), TOL[prec])
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_c2r_512cubed_full_size(prec):
+    """The c2r backward of the 512^3 workload over the whole array, in the benchmark's launch
+    configuration: (1) the closed-form half spectrum of the noise-free field must come back as
+    the field itself (its values on the grid, evaluated without any transform); (2) on the
+    noisy field, the c2r of the oracle's half spectrum against the oracle's own c2r."""
+    n = 512
+    shape = (n, n, n)
+    f, modes = synth.random_mode_field(shape, 5121, n_modes=64, noise=0.0, return_modes=True)
+    H = closed_form_half_spectrum(n, modes)
+    keys = list(H.keys())
+    Hd = torch.zeros((n, n, n // 2 + 1), dtype=torch.complex128, device="cuda")
+    idx = torch.tensor(keys, device="cuda").T
+    Hd[idx[0], idx[1], idx[2]] = torch.tensor([H[k] for k in keys], dtype=torch.complex128, device="cuda")
+    Hd = Hd.to(torch.complex64 if prec == "f32" else torch.complex128)
+    fd = torch.from_numpy(f).cuda()
+    with afft.Plan(shape, "r2c", prec) as p:
+        y = p.backward(Hd)
+        torch.cuda.synchronize()
+        err = float(torch.linalg.vector_norm(y.to(torch.float64) - fd) / torch.linalg.vector_norm(fd))
+        report("c2r 512^3 %s closed-form spectrum -> field" % prec, err, TOL[prec])
+        del y, Hd, fd
+        g = synth.random_mode_field(shape, 5121, n_modes=64, noise=1e-3).astype(RDT[prec])
+        G = oracle.r2c(g).astype(CDT[prec])
+        ref = oracle.c2r(G, n)
+        yb = p.backward(torch.from_numpy(G).cuda())
+        torch.cuda.synchronize()
+        report("c2r 512^3 %s vs oracle c2r (noisy field)" % prec, oracle.rel_l2(yb.cpu().numpy(), ref), TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_c2c_512cubed_full_size(prec):
+    """512^3 c2c over the whole array.  (1) A sum of 64 complex plane waves c_m exp(+i k_m.x):
+    the forward spectrum is exactly N c_m at k_m and zero elsewhere.  (2) The splitmix64 input
+    of the c2c workload, forward against the oracle's full 3-D transform, and the backward
+    transform of the oracle's spectrum against the oracle's backward transform."""
+    n = 512
+    shape = (n, n, n)
+    N = float(n) ** 3
+    tdt = torch.complex64 if prec == "f32" else torch.complex128
+    ks, amp, phase = synth.draw_modes(shape, 64, 5122)
+    coef = amp * np.exp(1j * phase)
+    spec = {}
+    for k, c in zip(ks, coef):
+        key = tuple(int(v) % n for v in k)
+        spec[key] = spec.get(key, 0) + N * c
+    keys = list(spec.keys())
+    idx = torch.tensor(keys, device="cuda").T
+    vals = torch.tensor([spec[k] for k in keys], dtype=torch.complex128, device="cuda")
+    x = synth.plane_wave_sum_torch(shape, ks, coef).to(tdt)
+    with afft.Plan(shape, "c2c", prec) as p:
+        assert p.describe()["blocked"] == 0   # the benchmark's row-major stages
+        X = p.forward(x)
+        torch.cuda.synchronize()
+        Xe = X.to(torch.complex128, copy=True)
+        Xe[idx[0], idx[1], idx[2]] -= vals
+        report("c2c 512^3 %s plane waves vs closed form" % prec,
+               float(torch.linalg.vector_norm(Xe) / torch.linalg.vector_norm(vals)), TOL[prec])
+        del Xe
+        y = p.backward(X)
+        torch.cuda.synchronize()
+        x64 = x.to(torch.complex128)
+        report("c2c 512^3 %s round trip" % prec,
+               float(torch.linalg.vector_norm(y.to(torch.complex128) - x64) / torch.linalg.vector_norm(x64)),
+               TOL[prec])
+        del X, y, x, x64
+        t = torch.empty(shape, dtype=tdt, device="cuda")
+        afft.fill_uniform(t, 5120)
+        xh = t.cpu().numpy()
+        ref = oracle.c2c(xh, -1, "fft")
+        Xg = p.forward(t)
+        torch.cuda.synchronize()
+        report("c2c 512^3 %s forward vs oracle (splitmix input)" % prec,
+               oracle.rel_l2(Xg.cpu().numpy(), ref), TOL[prec])
+        del Xg, t, xh
+        R = ref.astype(CDT[prec])
+        refb = oracle.c2c(R, +1, "fft")
+        yb = p.backward(torch.from_numpy(R).cuda())
+        torch.cuda.synchronize()
+        report("c2c 512^3 %s backward vs oracle" % prec, oracle.rel_l2(yb.cpu().numpy(), refb), TOL[prec])
+
+
 # --- the large c2c configuration: 1024^3 complex64 ------------------------------------
 
 def test_c2c_1024_subcase_256cubed_splitmix_input():
@@ -267,38 +349,41 @@ def test_c2c_1024_subcase_256cubed_splitmix_input():
     report("c2c 256^3 f32 (1024^3 sub-case)", oracle.rel_l2(X.cpu().numpy(), ref), TOL["f32"])
 
 
-def test_c2c_1024cubed_full_size_properties():
-    """1024^3 complex64 (8 GB): round trip and Parseval on the splitmix input, and a plane
-    wave that must come out as a single delta of height N."""
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_c2c_1024cubed_full_size_properties(prec):
+    """1024^3 c2c (8.6 GB complex64, 17.2 GB complex128) in the default launch configuration,
+    the blocked layout: round trip and Parseval on the splitmix input, and a plane wave that must
+    come out as a single delta of height N with no leakage anywhere else in the array."""
     n = 1024
     shape = (n, n, n)
     N = float(n) ** 3
-    x = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    tdt = torch.complex64 if prec == "f32" else torch.complex128
+    x = torch.empty(shape, dtype=tdt, device="cuda")
     afft.fill_uniform(x, 10240)
-    with afft.Plan(shape, "c2c", "f32") as p:
+    with afft.Plan(shape, "c2c", prec) as p:
+        assert p.describe()["blocked"] == 1
         X = p.forward(x)
         torch.cuda.synchronize()
         px = float(torch.sum(torch.abs(x.to(torch.complex128)) ** 2))
         pX = float(torch.sum(torch.abs(X.to(torch.complex128)) ** 2))
-        report("c2c 1024^3 f32 Parseval", abs(pX / (N * px) - 1), TOL["f32"])
+        report("c2c 1024^3 %s Parseval" % prec, abs(pX / (N * px) - 1), TOL[prec])
         y = p.backward(X)
         torch.cuda.synchronize()
+        del X
         rt = float(torch.linalg.vector_norm((y - x).to(torch.complex128)) / torch.linalg.vector_norm(x.to(torch.complex128)))
-        report("c2c 1024^3 f32 round trip", rt, TOL["f32"])
-        del X, y
+        report("c2c 1024^3 %s round trip" % prec, rt, TOL[prec])
+        del y
         k = (3, 1000, 17)
         j = torch.arange(n, device="cuda", dtype=torch.float64)
         e = [torch.exp(2j * np.pi * torch.remainder(j * kk, n) / n) for kk in k]
-        pw = (e[0][:, None, None] * e[1][None, :, None] * e[2][None, None, :]).to(torch.complex64)
-        x.copy_(pw)
-        del pw
+        x.copy_(e[0][:, None, None] * e[1][None, :, None] * e[2][None, None, :])
         X = p.forward(x)
         torch.cuda.synchronize()
         peak = complex(X[k].item())
         X[k] = 0
         rest = float(torch.linalg.vector_norm(X.to(torch.complex128)))
-        report("c2c 1024^3 f32 plane-wave peak", abs(peak - N) / N, TOL["f32"])
-        report("c2c 1024^3 f32 plane-wave leakage", rest / N, TOL["f32"])
+        report("c2c 1024^3 %s plane-wave peak" % prec, abs(peak - N) / N, TOL[prec])
+        report("c2c 1024^3 %s plane-wave leakage" % prec, rest / N, TOL[prec])
 
 
 def test_c2c_1024_point_rows_megabytes_apart_separable_input():
