@@ -8,9 +8,12 @@ so no explicit flush is needed between steps.
 
 value = whole-job algorithmic bytes per second as a percentage of one GB300's
 measured HBM bandwidth (MEASURED_PEAKS.json), the algorithmic bytes being
-the 3-pass minimum: one full-array read and write per axis stage.  At N GPUs
-every rank runs its own independent replica (the transform does not shard
-without an all-to-all), and the percentages add up (weak scaling).
+the 3-pass minimum: one full-array read and write per axis stage.  At N > 1
+GPUs the one 512^3 transform is distributed in slabs of 512/N planes (the
+paper's slab decomposition, Algorithm 3: N2 and N1 stages per rank, one NCCL
+all-to-all, the N0 stage), so the total work is fixed (strong scaling);
+`--decomp replicas` instead runs an independent transform per GPU (weak
+scaling), and `--decomp slab` runs the slab path even on one GPU.
 
 The default line also carries, under "also", the metric's other
 configurations measured in the same run: r2c 512^3 FP64, c2c 512^3 FP32/FP64,
@@ -277,17 +280,24 @@ def run_gpu(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    decomp = args.decomp or ("slab" if world > 1 else "plan")
+    if world > 1 or decomp == "slab":
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29517")
+        os.environ.setdefault("RANK", str(rank))
+        os.environ.setdefault("WORLD_SIZE", str(world))
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     if rank == 0:
         libbuild.build()
-    if world > 1:
+    if dist.is_initialized():
         dist.barrier()
     afft.load()
+    if decomp == "slab":
+        return run_slab(args, world, rank, local)
 
     def barrier():
-        if world > 1:
+        if dist.is_initialized():
             dist.barrier()
         torch.cuda.synchronize()
 
@@ -385,9 +395,121 @@ def run_gpu(args):
         line["cpu_baseline"] = cpu_baseline_block(step_bytes, peak)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
+    if dist.is_initialized():
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_slab(args, world, rank, local):
+    """The 512^3 r2c + c2r step distributed in slabs over the ranks (Algorithm 3): rank r holds
+    planes r 512/N ...; forward = N2 and N1 stages, NCCL all-to-all, N0 stage (its output block
+    is all k0, rows r 512/N ..., all k2); backward the reverse.  Strong scaling: the whole job is
+    one transform."""
+    import torch
+    import torch.distributed as dist
+    from paper_1506_07933_gb300 import slab
+
+    peak, peak_kind = peaks()
+    prec = args.precision
+    real_b, cplx_b = (4, 8) if prec == "f32" else (8, 16)
+    f = slab.SlabFFT(SHAPE, "r2c", prec)
+    field = cpu_field() if prec == "f32" else cpu_field().astype("float64")
+    mine = field[rank * f.n0p:(rank + 1) * f.n0p]
+    x = torch.from_numpy(mine.copy()).cuda()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return f.backward(f.forward(x))
+
+    def barrier():
+        dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    zy, xp = f.engine.zy, f.engine.x
+    zy.timing_begin(2 * args.steps)
+    xp.timing_begin(2 * args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        t_begin = time.time()
+        e0.record(stream)
+        for _ in range(args.steps):
+            y = step()
+        e1.record(stream)
+        barrier()
+        t_end = time.time()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dist, "cuda")
+    # this rank's stage kernels: records alternate forward / backward; zy slots (N2, N1, -) forward
+    # and (-, N1, N2) backward, x slots (-, -, N0) forward and (N0, -, -) backward
+    tz, tx = zy.timing_end(), xp.timing_end()
+    nh = SHAPE[2] // 2 + 1
+    local_planes = f.n0p * SHAPE[1]
+    b_z = local_planes * (SHAPE[2] * real_b + nh * cplx_b)
+    b_y = 2 * local_planes * nh * cplx_b
+    b_x = 2 * SHAPE[0] * f.n1p * nh * cplx_b
+    dz, dx = zy.describe(), xp.describe()
+    cand = []
+    for i, r in enumerate(tz):
+        fw = i % 2 == 0
+        cand.append(("N2 " + ("fwd" if fw else "bwd"), dz["stage_kernels_forward" if fw else "stage_kernels_backward"][0 if fw else 2],
+                     r[0] if fw else r[2], b_z))
+        cand.append(("N1 " + ("fwd" if fw else "bwd"), dz["stage_kernels_forward"][1], r[1], b_y))
+    for i, r in enumerate(tx):
+        fw = i % 2 == 0
+        cand.append(("N0 " + ("fwd" if fw else "bwd"), dx["stage_kernels_forward"][2], r[2] if fw else r[0], b_x))
+    stages = {}
+    for name, kern, t, b in cand:
+        stages.setdefault((name, kern, b), []).append(t)
+    means = [(sum(v) / len(v), name, kern, b) for (name, kern, b), v in stages.items()]
+    t_dom, name_dom, kern_dom, b_dom = max(means)
+    roofline = {"bound": "hbm", "achieved": b_dom / (t_dom * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": b_dom / (t_dom * 1e-3) / 1e9 / peak, "traffic": None, "kernel": kern_dom,
+                "stage": name_dom + " (rank 0's slab)", "peak_source": peak_kind, "bytes_per_launch": b_dom,
+                "mean_launch_ms": t_dom}
+    xd = x.double()
+    round_trip = float(torch.linalg.vector_norm(y.double() - xd) / torch.linalg.vector_norm(xd))
+    step_bytes = 2 * sum(workload_bytes(SHAPE, real_b, cplx_b))
+    value = whole_job_percent(step_bytes, 1, ms, peak)
+    # end to end: each rank uploads its slab from pinned memory and reads its result back
+    hx = torch.from_numpy(mine.copy()).pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    for _ in range(2):
+        x.copy_(hx, non_blocking=True)
+        hy.copy_(step(), non_blocking=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        x.copy_(hx, non_blocking=True)
+        hy.copy_(step(), non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dist, "cuda")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": WORKLOAD % {"f32": "float32", "f64": "float64"}[prec],
+                   "l2": "inputs larger than L2 in total, no flush", "bytes_per_step": step_bytes,
+                   "parallelism": "slab decomposition x%d (NCCL all-to-all)" % world},
+        "round_trip_rel_l2": round_trip,
+        "e2e": {"value": whole_job_percent(step_bytes, 1, e2e_ms, peak), "unit": UNIT,
+                "h2d_bytes_per_step": hx.numel() * hx.element_size() * world,
+                "d2h_bytes_per_step": hy.numel() * hy.element_size() * world, "ms_per_step": e2e_ms,
+                "call": "SlabFFT.forward + backward with the slab copied in and out (torch copies)"},
+        "gpu_launches": args.steps * (f.engine.zy.launches(False) + f.engine.zy.launches(True)
+                                      + f.engine.x.launches(False) + f.engine.x.launches(True)),
+        "clocks": clk.summary(t_begin, t_end),
+        "roofline": roofline,
+        "stages": [{"stage": n, "kernel": k, "mean_ms": round(t, 5), "bytes": b} for t, n, k, b in sorted(means)],
+    }
+    f.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
 
 
 def measure_e2e(args, plan, field, x, X, y, stream, barrier, world, step_bytes, peak, torch, dist):
@@ -665,6 +787,9 @@ def main():
                     help="leave out the metric's other configurations (the 'also' block)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--decomp", choices=["plan", "slab", "replicas"], default=None,
+                    help="one plan per GPU at N = 1 (default), slab decomposition (default at N > 1) "
+                         "or independent replicas per GPU")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

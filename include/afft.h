@@ -83,7 +83,8 @@ enum {
     AFFT_ERR_CUDA = 8,        /* a CUDA call or kernel launch failed           */
     AFFT_ERR_UNSUPPORTED = 9, /* valid request this version does not implement */
     AFFT_ERR_SCRATCH = 10,    /* afft_c2r_noalloc: the transform does not fit its fixed scratch */
-    AFFT_ERR_TIMEOUT = 11     /* a kernel gave up a bounded wait (see afft_plan_device_status) */
+    AFFT_ERR_TIMEOUT = 11,    /* a kernel gave up a bounded wait (see afft_plan_device_status) */
+    AFFT_ERR_AXES = 12        /* axes mask empty or out of range, or r2c without axis 2  */
 };
 
 /*
@@ -114,6 +115,49 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
  * AFFT_ERR_SIZE; input/output byte counts below include the batch.
  */
 int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch, int kind, int precision);
+
+/*
+ * A plan that transforms only some of the three axes: bit a of `axes` (1, 2, 4
+ * for n[0], n[1], n[2]) selects axis a.  These are the building blocks of the
+ * paper's distributed forms, where each process runs the 1-D FFT stages of the
+ * axes it holds whole and exchanges data in between: the slab decomposition
+ * (Algorithm 3) runs axes {1, 2} on its n0/P planes and, after the all-to-all,
+ * axis {0} on its n1/P rows; the d-dimensional transform (Algorithm 2) runs a
+ * batched 3-D plan on the trailing axes and a {0} plan on the leading one.
+ * Layouts are those of afft_plan_create_batched; a transformed axis needs a
+ * 2/3/5-smooth length, an untransformed one only n[a] >= 1.  An R2C plan must
+ * include axis 2 (the halved axis, AFFT_ERR_AXES otherwise).  The forward
+ * transform runs the selected stages in Algorithm 1's order (N2, N1, N0) and
+ * the backward one in reverse, multiplied by 1 / (product of the transformed
+ * n[a]) unless afft_plan_set_backward_scale says otherwise.  With axis 2
+ * untransformed the factor costs a separate pass over the output when it is
+ * not 1.  axes = 7 is afft_plan_create_batched.  The L2 slab schedule, the
+ * blocked layout and the Poisson solve need axes = 7 (AFFT_ERR_AXES from
+ * afft_execute_poisson otherwise).
+ */
+int afft_plan_create_axes(afft_plan **out, const int64_t n[3], int64_t batch, int kind, int precision, int axes);
+
+/*
+ * The factor the backward transform multiplies its result by (default 1 / N of
+ * the transformed axes, the normalisation of Section 2, footnote 2).  A
+ * distributed transform sets 1 / N_global on the plan that runs last and 1 on
+ * the others, so that the whole backward transform carries 1/N exactly once.
+ * AFFT_ERR_SIZE for 0 or NaN.  Not while the plan is in use on a stream.
+ */
+int afft_plan_set_backward_scale(afft_plan *p, double scale);
+double afft_plan_backward_scale(const afft_plan *p);   /* 0 for NULL */
+
+/*
+ * rows x width bytes from src (row pitch spitch bytes) to dst (pitch dpitch),
+ * asynchronous on the stream (cudaMemcpy2DAsync, any memory kind).  The pack
+ * and unpack of the slab decomposition's all-to-all (Algorithm 3; the paper's
+ * pack/unpack kernels of Section 2) are such copies: the n0/P x n1/P x n2h
+ * block bound for each process is n0/P rows of n1/P * n2h elements, n1 * n2h
+ * elements apart.  AFFT_ERR_SIZE if width exceeds a pitch; nothing to do for
+ * zero rows or width.
+ */
+int afft_copy_2d(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t rows,
+                 void *cuda_stream);
 
 /*
  * Forward transform (Algorithm 1, left column): 1-D FFTs along N2, then N1,

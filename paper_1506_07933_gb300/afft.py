@@ -29,7 +29,7 @@ PRECISIONS = {"f32": F32, "f64": F64, "f32_split": F32_SPLIT}
 STATUS = {
     0: "AFFT_OK", 1: "AFFT_ERR_NULL", 2: "AFFT_ERR_SIZE", 3: "AFFT_ERR_R2C_ODD", 4: "AFFT_ERR_KIND",
     5: "AFFT_ERR_PRECISION", 6: "AFFT_ERR_NOMEM", 7: "AFFT_ERR_INPLACE", 8: "AFFT_ERR_CUDA",
-    9: "AFFT_ERR_UNSUPPORTED", 10: "AFFT_ERR_SCRATCH", 11: "AFFT_ERR_TIMEOUT",
+    9: "AFFT_ERR_UNSUPPORTED", 10: "AFFT_ERR_SCRATCH", 11: "AFFT_ERR_TIMEOUT", 12: "AFFT_ERR_AXES",
 }
 
 # Every symbol include/afft.h declares.
@@ -42,7 +42,8 @@ EXPORTS = [
     "afft_plan_device_status", "afft_plan_set_l2_chunk", "afft_plan_l2_chunk",
     "afft_plan_create_batched", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
     "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe",
-    "afft_plan_set_blocked", "afft_plan_get_tuning", "afft_plan_set_tuning",
+    "afft_plan_set_blocked", "afft_plan_get_tuning", "afft_plan_set_tuning", "afft_plan_create_axes",
+    "afft_plan_set_backward_scale", "afft_plan_backward_scale", "afft_copy_2d",
 ]
 
 _lib = None
@@ -66,6 +67,11 @@ def load(path: str = None):
     vp, i64p, c_int, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_size_t
     lib.afft_plan_create.argtypes = [ctypes.POINTER(vp), i64p, c_int, c_int]
     lib.afft_plan_create_batched.argtypes = [ctypes.POINTER(vp), i64p, ctypes.c_int64, c_int, c_int]
+    lib.afft_plan_create_axes.argtypes = [ctypes.POINTER(vp), i64p, ctypes.c_int64, c_int, c_int, c_int]
+    lib.afft_plan_set_backward_scale.argtypes = [vp, ctypes.c_double]
+    lib.afft_plan_backward_scale.argtypes = [vp]
+    lib.afft_plan_backward_scale.restype = ctypes.c_double
+    lib.afft_copy_2d.argtypes = [vp, sz, vp, sz, sz, sz, vp]
     lib.afft_plan_tune.argtypes = [vp, vp]
     lib.afft_execute_poisson.argtypes = [vp, vp, vp, vp]
     lib.afft_plan_describe.argtypes = [vp, ctypes.c_char_p, sz]
@@ -101,7 +107,8 @@ def load(path: str = None):
               "afft_plan_timing_end", "afft_c2r_noalloc", "afft_plan_device_status",
               "afft_plan_set_l2_chunk", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
               "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe",
-              "afft_plan_set_blocked", "afft_plan_get_tuning", "afft_plan_set_tuning"):
+              "afft_plan_set_blocked", "afft_plan_get_tuning", "afft_plan_set_tuning", "afft_plan_create_axes",
+              "afft_plan_set_backward_scale", "afft_copy_2d"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -137,6 +144,20 @@ def afft_plan_create_batched(shape, batch: int, kind: int, precision: int) -> ct
     _check(load().afft_plan_create_batched(ctypes.byref(p), n, int(batch), int(kind), int(precision)),
            "afft_plan_create_batched")
     return p
+
+
+def afft_plan_create_axes(shape, batch: int, kind: int, precision: int, axes: int) -> ctypes.c_void_p:
+    n = (ctypes.c_int64 * 3)(*[int(s) for s in shape])
+    p = ctypes.c_void_p()
+    _check(load().afft_plan_create_axes(ctypes.byref(p), n, int(batch), int(kind), int(precision), int(axes)),
+           "afft_plan_create_axes")
+    return p
+
+
+def afft_copy_2d(dst_ptr: int, dpitch: int, src_ptr: int, spitch: int, width: int, rows: int, stream: int) -> None:
+    """rows x width bytes between pitched buffers (cudaMemcpy2DAsync on the stream)."""
+    _check(load().afft_copy_2d(dst_ptr, int(dpitch), src_ptr, int(spitch), int(width), int(rows), stream),
+           "afft_copy_2d")
 
 
 def afft_execute_forward(plan, in_ptr: int, out_ptr: int, stream: int) -> None:
@@ -184,17 +205,24 @@ class Plan:
     ``forward(x)``: unscaled forward transform (c2c: complex -> complex;
     r2c: real [n0, n1, n2] -> complex [n0, n1, n2 // 2 + 1]).
     ``backward(X)``: inverse scaled by 1/N (c2c, or c2r for an r2c plan).
+    ``batch``: that many transforms stored back to back.  ``axes``: a bit mask
+    (1, 2, 4 for n0, n1, n2) of the axes to transform, for the building blocks
+    of the slab and d-dimensional transforms (see afft_plan_create_axes).
     Tensors must be contiguous, on the plan's device, of the plan's dtype.
     Calls are asynchronous on the current (or given) stream.
     """
 
-    def __init__(self, shape, kind="c2c", precision="f32", batch=None):
+    def __init__(self, shape, kind="c2c", precision="f32", batch=None, axes=None):
         self.shape = tuple(int(s) for s in shape)
         self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.batch = batch
-        if batch is None:
+        self.axes = 7 if axes is None else int(axes)
+        if axes is not None:
+            self._p = afft_plan_create_axes(self.shape, 1 if batch is None else int(batch), self.kind,
+                                            self.precision, self.axes)
+        elif batch is None:
             self._p = afft_plan_create(self.shape, self.kind, self.precision)
         else:
             self._p = afft_plan_create_batched(self.shape, int(batch), self.kind, self.precision)
@@ -284,6 +312,14 @@ class Plan:
                 raise ValueError("%s must be a contiguous CPU tensor %s %s" % (w, dt, shape))
         afft_execute_backward_host(self._p, host_in.data_ptr(), host_out.data_ptr(), dev_in.data_ptr(),
                                    dev_out.data_ptr(), _stream_handle(stream))
+
+    @property
+    def backward_scale(self) -> float:
+        return float(load().afft_plan_backward_scale(self._p))
+
+    def set_backward_scale(self, scale: float) -> None:
+        """The factor of the backward transform (default 1 / product of the transformed n)."""
+        _check(load().afft_plan_set_backward_scale(self._p, float(scale)), "afft_plan_set_backward_scale")
 
     def set_blocked(self, on: bool) -> None:
         """Blocked c2c layout (a workspace of the array's size; see afft_plan_set_blocked)."""

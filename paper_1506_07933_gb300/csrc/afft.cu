@@ -55,6 +55,8 @@ struct afft_plan {
     int64_t batch;         // transforms per execute, stored back to back
     int kind;
     int precision;
+    int axes;              // bit a set: axis a is transformed (7: the full 3-D transform)
+    double bscale;         // factor of the backward transform (default 1 / prod of transformed n_a)
     int64_t nh;            // last-axis length of the complex array: n2 (C2C) or n2/2+1 (R2C)
     AxisPlan ax[3];        // ax[2] transforms the contiguous axis (length n2, or n2/2 for R2C)
     int post_off;          // R2C: offset of the w_{n2}^k table (n2/2+1 entries)
@@ -705,7 +707,7 @@ cudaError_t axis_stage(afft_plan *p, int a, const V *in, V *out, long long outer
 // Whether the plan's shapes allow the blocked layout (not whether it is worth it).
 bool blocked_eligible(const afft_plan *p)
 {
-    if (p->kind != AFFT_C2C || p->n[0] < 2) return false;
+    if (p->kind != AFFT_C2C || p->n[0] < 2 || p->axes != 7) return false;
     for (int a = 0; a < 3; ++a)
         if (p->four[a].on) return false;
     const AxisPlan &x = p->ax[0], &y = p->ax[1], &z = p->ax[2];
@@ -766,7 +768,7 @@ int run_blocked(afft_plan *p, const void *in, void *out, int backward, cudaStrea
     z.desc.blk_out = 1;
     z.desc.blk_n1 = n1;
     z.desc.blk_planes = P0;
-    const double scale = backward ? 1.0 / ((double)n0 * (double)n1 * (double)n2) : 1.0;
+    const double scale = backward ? p->bscale : 1.0;
     mark(p, 0, s);
     if (contig<V>(z, (const V *)in, ws, tw, P0 * n1, backward, scale, s) != cudaSuccess) return AFFT_ERR_CUDA;
     mark(p, 1, s);
@@ -788,6 +790,102 @@ bool use_blocked(const afft_plan *p)
     return p->blocked && p->chunk_planes == 0 && blocked_eligible(p);
 }
 
+// x *= scale over `count` complex values (the backward normalisation of plans whose last
+// backward stage is a strided one, i.e. plans that leave the contiguous axis untransformed).
+template <typename V>
+__global__ void k_scale(V *x, long long count, double scale)
+{
+    using T = decltype(V().x);
+    const T sc = (T)scale;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        V v = x[i];
+        v.x *= sc;
+        v.y *= sc;
+        x[i] = v;
+    }
+}
+
+// Forward transform of a plan over a subset of the axes (Algorithm 1's stages for the selected
+// axes only, in its order N2, N1, N0): the first stage that runs reads `in`, every stage writes
+// `out`; with no stage to run, `in` is copied to `out`.
+template <typename V>
+int run_forward_axes(afft_plan *p, const void *in, void *out, cudaStream_t s)
+{
+    using T = decltype(V().x);
+    const V *tw = (const V *)p->d_tw;
+    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh, B = p->batch, P0 = B * n0;
+    const V *src = (const V *)in;
+    V *w = (V *)out;
+    mark(p, 0, s);
+    if (p->axes & 4) {
+        cudaError_t e;
+        if (p->kind == AFFT_C2C && p->four[2].on) e = axis_stage<V>(p, 2, src, w, P0 * n1, 1, 0, 1.0, s);
+        else if (p->kind == AFFT_C2C) e = contig<V>(p->ax[2], src, w, tw, P0 * n1, 0, 1.0, s);
+        else e = r2c<V, T>(p->ax[2], (const T *)in, w, tw, tw + p->post_off, P0 * n1, s);
+        if (e != cudaSuccess) return AFFT_ERR_CUDA;
+        src = w;
+    }
+    mark(p, 1, s);
+    if ((p->axes & 2) && n1 > 1) {
+        if (axis_stage<V>(p, 1, src, w, P0, nh, 0, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        src = w;
+    }
+    mark(p, 2, s);
+    if ((p->axes & 1) && n0 > 1) {
+        if (axis_stage<V>(p, 0, src, w, B, n1 * nh, 0, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        src = w;
+    }
+    if (src != w && cudaMemcpyAsync(w, src, (size_t)P0 * n1 * nh * sizeof(V), cudaMemcpyDeviceToDevice, s) !=
+                        cudaSuccess)
+        return AFFT_ERR_CUDA;
+    mark(p, 3, s);
+    return AFFT_OK;
+}
+
+// Backward transform over a subset of the axes: N0, N1, N2 among the selected ones, then the
+// plan's backward factor (folded into the contiguous stage, else a separate scaling pass when
+// the factor is not 1).  r2c plans always include the contiguous axis (their c2r).
+template <typename V>
+int run_backward_axes(afft_plan *p, const void *in, void *out, cudaStream_t s)
+{
+    using T = decltype(V().x);
+    const V *tw = (const V *)p->d_tw;
+    const long long n0 = p->n[0], n1 = p->n[1], nh = p->nh, B = p->batch, P0 = B * n0;
+    const long long count = P0 * n1 * nh;
+    V *buf = p->kind == AFFT_C2C ? (V *)out : (V *)p->d_work;
+    const V *src = (const V *)in;
+    mark(p, 0, s);
+    if ((p->axes & 1) && n0 > 1) {
+        if (axis_stage<V>(p, 0, src, buf, B, n1 * nh, 1, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        src = buf;
+    }
+    mark(p, 1, s);
+    if ((p->axes & 2) && n1 > 1) {
+        if (axis_stage<V>(p, 1, src, buf, P0, nh, 1, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+        src = buf;
+    }
+    mark(p, 2, s);
+    if (p->axes & 4) {
+        cudaError_t e;
+        if (p->kind == AFFT_C2C && p->four[2].on) e = axis_stage<V>(p, 2, src, (V *)out, P0 * n1, 1, 1, p->bscale, s);
+        else if (p->kind == AFFT_C2C) e = contig<V>(p->ax[2], src, (V *)out, tw, P0 * n1, 1, p->bscale, s);
+        else e = c2r<V, T>(p->ax[2], src, (T *)out, tw, tw + p->post_off, P0 * n1, p->bscale, s);
+        if (e != cudaSuccess) return AFFT_ERR_CUDA;
+    } else {
+        if (src != (const V *)out &&
+            cudaMemcpyAsync(out, src, (size_t)count * sizeof(V), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return AFFT_ERR_CUDA;
+        if (p->bscale != 1.0) {
+            const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((count + 255) / 256, 152LL * 16));
+            k_scale<V><<<blocks, 256, 0, s>>>((V *)out, count, p->bscale);
+            if (cudaGetLastError() != cudaSuccess) return AFFT_ERR_CUDA;
+        }
+    }
+    mark(p, 3, s);
+    return AFFT_OK;
+}
+
 // Forward: N2 stage (c2c, or r2c), N1 stage, N0 stage, all writing `out`.
 // With chunk_planes > 0 the N2 and N1 stages run slab by slab: N2 of slab c on
 // the caller's stream, N1 of slab c on the plan's second stream right after, so
@@ -797,6 +895,7 @@ template <typename V>
 int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     if (use_blocked(p)) return run_blocked<V>(p, in, out, 0, s);
+    if (p->axes != 7) return run_forward_axes<V>(p, in, out, s);
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
     const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, B = p->batch;
@@ -854,11 +953,12 @@ template <typename V>
 int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
 {
     if (use_blocked(p)) return run_blocked<V>(p, in, out, 1, s);
+    if (p->axes != 7) return run_backward_axes<V>(p, in, out, s);
     using T = decltype(V().x);
     const V *tw = (const V *)p->d_tw;
     const long long n0 = p->n[0], n1 = p->n[1], n2 = p->n[2], nh = p->nh, B = p->batch;
     const long long P0 = B * n0;
-    const double scale = 1.0 / ((double)p->n[0] * (double)p->n[1] * (double)p->n[2]);
+    const double scale = p->bscale;
     // C2C works in `out`; c2r works in the plan's workspace and writes real `out` last.
     V *buf = p->kind == AFFT_C2C ? (V *)out : (V *)p->d_work;
     const long long plane_w = n1 * nh, plane_out = n1 * n2;
@@ -913,7 +1013,7 @@ int configure_chunks(afft_plan *p, size_t bytes)
     p->chunk_planes = 0;
     const long long n0 = p->batch * p->n[0], n1 = p->n[1];
     const size_t plane = (size_t)n1 * p->nh * cplx_size(p->precision);
-    if (bytes == 0 || n1 <= 1 || n0 < 3 || plane == 0) return AFFT_OK;
+    if (bytes == 0 || n1 <= 1 || n0 < 3 || plane == 0 || p->axes != 7) return AFFT_OK;
     long long K = (long long)(bytes / plane);
     if (K < 1) K = 1;
     if (K * 2 >= n0) return AFFT_OK;  // fewer than three slabs: nothing to gain
@@ -1052,6 +1152,7 @@ const char *afft_status_string(int status)
     case AFFT_ERR_UNSUPPORTED: return "not supported by this version";
     case AFFT_ERR_SCRATCH: return "transform exceeds the fixed no-allocation scratch array";
     case AFFT_ERR_TIMEOUT: return "a kernel's bounded wait ran out (asynchronous copy never completed)";
+    case AFFT_ERR_AXES: return "axes must be a nonzero subset of {0, 1, 2}, including axis 2 for r2c";
     default: return "unknown status";
     }
 }
@@ -1063,14 +1164,22 @@ int afft_plan_create(afft_plan **out, const int64_t n[3], int kind, int precisio
 
 int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch, int kind, int precision)
 {
+    return afft_plan_create_axes(out, n, batch, kind, precision, 7);
+}
+
+int afft_plan_create_axes(afft_plan **out, const int64_t n[3], int64_t batch, int kind, int precision, int axes)
+{
     if (!out) return AFFT_ERR_NULL;
     *out = nullptr;
     if (!n) return AFFT_ERR_NULL;
     if (kind != AFFT_C2C && kind != AFFT_R2C) return AFFT_ERR_KIND;
     if (precision != AFFT_F32 && precision != AFFT_F64 && precision != AFFT_F32_SPLIT)
         return AFFT_ERR_PRECISION;
+    if (axes < 1 || axes > 7) return AFFT_ERR_AXES;
+    if (kind == AFFT_R2C && !(axes & 4)) return AFFT_ERR_AXES;   // r2c halves the contiguous axis
+    // transformed axes need 2/3/5-smooth lengths; the others only a length
     for (int i = 0; i < 3; ++i)
-        if (!factor_ok(n[i])) return AFFT_ERR_SIZE;
+        if (((axes >> i) & 1) ? !factor_ok(n[i]) : n[i] < 1) return AFFT_ERR_SIZE;
     if (kind == AFFT_R2C && n[2] % 2 != 0) return AFFT_ERR_R2C_ODD;
     if (batch < 1) return AFFT_ERR_SIZE;
     const int64_t zlen = kind == AFFT_R2C ? n[2] / 2 : n[2];
@@ -1081,7 +1190,8 @@ int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch,
     {
         const int64_t len0[3] = {n[0], n[1], zlen};
         for (int a = 0; a < 3; ++a)
-            if (len0[a] > kMaxLine && !four_step_split(len0[a], split_a[a], split_b[a])) return AFFT_ERR_UNSUPPORTED;
+            if (((axes >> a) & 1) && len0[a] > kMaxLine && !four_step_split(len0[a], split_a[a], split_b[a]))
+                return AFFT_ERR_UNSUPPORTED;
     }
 
     afft_plan *p = new (std::nothrow) afft_plan();
@@ -1090,6 +1200,10 @@ int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch,
     p->batch = batch;
     p->kind = kind;
     p->precision = precision;
+    p->axes = axes;
+    p->bscale = 1.0;
+    for (int i = 0; i < 3; ++i)
+        if ((axes >> i) & 1) p->bscale /= (double)n[i];
     p->nh = kind == AFFT_R2C ? n[2] / 2 + 1 : n[2];
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         delete p;
@@ -1097,7 +1211,8 @@ int afft_plan_create_batched(afft_plan **out, const int64_t n[3], int64_t batch,
     }
 
     std::vector<int> tm, tl;
-    const int64_t len[3] = {n[0], n[1], zlen};
+    // an axis left untransformed gets the length-1 (copy) family, which its stage never launches
+    const int64_t len[3] = {(axes & 1) ? n[0] : 1, (axes & 2) ? n[1] : 1, (axes & 4) ? zlen : 1};
     bool any_four = false;
     for (int a = 0; a < 3; ++a) {
         FourStep &f = p->four[a];
@@ -1219,6 +1334,7 @@ int afft_execute_poisson(afft_plan *p, const void *in, void *out, void *stream)
 {
     if (!p || !in || !out) return AFFT_ERR_NULL;
     if (p->kind != AFFT_R2C) return AFFT_ERR_KIND;
+    if (p->axes != 7) return AFFT_ERR_AXES;
     if (in == out) return AFFT_ERR_INPLACE;
     const size_t nb = in_bytes(p);
     if (overlaps(in, nb, out, nb)) return AFFT_ERR_INPLACE;
@@ -1499,14 +1615,17 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
     const long long W1 = p->nh, W0 = p->n[1] * p->nh;
     const char *zf = p->four[2].on ? "k_strided+k_fourstep" : p->kind == AFFT_R2C ? "k_r2c" : "k_contig";
     const char *zb = p->four[2].on ? "k_strided+k_fourstep" : p->kind == AFFT_R2C ? "k_c2r" : "k_contig";
-    const char *y = blk ? "k_strided_pipe" : p->four[1].on ? "k_strided+k_fourstep" : strided_kernel_name(p, 1, W1);
-    const char *x = blk ? "k_strided_pipe" : p->four[0].on ? "k_strided+k_fourstep" : strided_kernel_name(p, 0, W0);
+    const char *y = !(p->axes & 2) || p->n[1] < 2 ? "none"
+                    : blk ? "k_strided_pipe" : p->four[1].on ? "k_strided+k_fourstep" : strided_kernel_name(p, 1, W1);
+    const char *x = !(p->axes & 1) || p->n[0] < 2 ? "none"
+                    : blk ? "k_strided_pipe" : p->four[0].on ? "k_strided+k_fourstep" : strided_kernel_name(p, 0, W0);
+    if (!(p->axes & 4)) zf = zb = "none";
     const int need = snprintf(
         buf, len,
         "{\"n\": [%lld, %lld, %lld], \"batch\": %lld, \"kind\": \"%s\", \"precision\": \"%s\", "
         "\"radix\": [\"%s\", \"%s\", \"%s\"], \"specialised\": [%d, %d, %d], \"four_step\": [%d, %d, %d], "
         "\"pipelined\": [%d, %d], \"contig_lines\": %d, \"strided_lines\": [%d, %d], "
-        "\"l2_slab_planes\": %d, \"blocked\": %d, "
+        "\"l2_slab_planes\": %d, \"blocked\": %d, \"axes\": %d, \"backward_scale\": %.17g, "
         "\"stage_kernels_forward\": [\"%s\", \"%s\", \"%s\"], \"stage_kernels_backward\": [\"%s\", \"%s\", \"%s\"]}",
         (long long)p->n[0], (long long)p->n[1], (long long)p->n[2], (long long)p->batch,
         p->kind == AFFT_C2C ? "c2c" : "r2c",
@@ -1514,7 +1633,7 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         !p->ax[0].ks->generic, !p->ax[1].ks->generic, !p->ax[2].ks->generic, p->four[0].on, p->four[1].on,
         p->four[2].on, p->ax[0].pipe, p->ax[1].pipe, p->ax[2].launch.lines,
         p->ax[0].pipe ? p->ax[0].ks->pipe_lines : p->ax[0].launch.lines,
-        p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, p->chunk_planes, (int)blk,
+        p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, p->chunk_planes, (int)blk, p->axes, p->bscale,
         blk ? "k_contig" : zf, y, x, x, y, blk ? "k_contig" : zb);
     if (need < 0) return AFFT_ERR_CUDA;
     return (size_t)need < len ? AFFT_OK : AFFT_ERR_SIZE;
@@ -1527,6 +1646,17 @@ size_t afft_plan_output_bytes(const afft_plan *p) { return p ? out_bytes(p) : 0;
 int afft_plan_launches(const afft_plan *p, int backward)
 {
     if (!p) return 0;
+    if (p->axes != 7) {
+        const int f0 = p->four[0].on, f1 = p->four[1].on, f2 = p->four[2].on && p->kind == AFFT_C2C;
+        int k = 0;
+        if ((p->axes & 1) && p->n[0] > 1) k += 1 + f0;
+        if ((p->axes & 2) && p->n[1] > 1) k += 1 + f1;
+        if (p->axes & 4) k += 1 + f2;
+        // a stage-less execution is one copy (not a kernel); a strided-only backward with a factor
+        // other than 1 adds the scaling kernel
+        if (backward && !(p->axes & 4) && p->bscale != 1.0) k += 1;
+        return k;
+    }
     const long long planes = p->batch * p->n[0];
     const long long slabs = p->chunk_planes > 0 ? (planes + p->chunk_planes - 1) / p->chunk_planes : 1;
     const int f0 = p->four[0].on, f1 = p->four[1].on, f2 = p->four[2].on && p->kind == AFFT_C2C;
@@ -1534,6 +1664,26 @@ int afft_plan_launches(const afft_plan *p, int backward)
     if (backward) return (int)(1 + f0 + slabs * (1 + f2 + y));
     const int x = p->n[0] > 1 ? 1 + f0 : 0;
     return (int)(slabs * (1 + f2 + y) + x);
+}
+
+int afft_plan_set_backward_scale(afft_plan *p, double scale)
+{
+    if (!p) return AFFT_ERR_NULL;
+    if (!(scale == scale) || scale == 0.0) return AFFT_ERR_SIZE;   // NaN or zero
+    p->bscale = scale;
+    return AFFT_OK;
+}
+
+double afft_plan_backward_scale(const afft_plan *p) { return p ? p->bscale : 0.0; }
+
+int afft_copy_2d(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t rows,
+                 void *stream)
+{
+    if (rows == 0 || width == 0) return AFFT_OK;
+    if (!dst || !src) return AFFT_ERR_NULL;
+    if (width > dpitch || width > spitch) return AFFT_ERR_SIZE;
+    return cuda_status(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDefault,
+                                         (cudaStream_t)stream));
 }
 
 int afft_plan_set_blocked(afft_plan *p, int on)

@@ -146,3 +146,28 @@ def test_noalloc_source_calls_no_allocator():
                  "malloc(", "new "):
         assert name not in code, name
     assert "cudaGetSymbolAddress" in code
+
+
+@pytest.mark.parametrize("n,kind,axes,code", [
+    ((8, 8, 8), 0, 0, 12),        # empty axis set
+    ((8, 8, 8), 0, 8, 12),        # bit beyond axis 2
+    ((8, 8, 8), 1, 3, 12),        # r2c without the halved contiguous axis
+    ((8, 8, 7), 0, 7, 2),         # a transformed axis must be 2/3/5-smooth
+    ((8, 8, 0), 0, 3, 2),         # an untransformed one must still have a length
+    ((7, 8, 9), 1, 6, 3),         # an untransformed n0 = 7 is fine, an odd r2c n2 is not
+])
+def test_plan_create_axes_rejects_bad_arguments(lib, n, kind, axes, code):
+    p = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * 3)(*n)
+    assert lib.afft_plan_create_axes(ctypes.byref(p), arr, 1, kind, 0, axes) == code
+    assert not p.value
+
+
+def test_backward_scale_and_copy_2d_argument_checks(lib):
+    assert lib.afft_plan_set_backward_scale(None, 1.0) == 1
+    assert lib.afft_plan_backward_scale(None) == 0.0
+    assert lib.afft_copy_2d(None, 16, None, 16, 8, 0, None) == 0      # nothing to copy
+    assert lib.afft_copy_2d(None, 16, None, 16, 8, 2, None) == 1
+    buf = ctypes.create_string_buffer(64)
+    assert lib.afft_copy_2d(buf, 8, buf, 16, 16, 2, None) == 2        # width beyond the pitch
+    assert afft.status_string(12) != "unknown status"
