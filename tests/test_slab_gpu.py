@@ -166,8 +166,10 @@ def test_fftn_4d_paper_size_plane_wave():
     k = (5, 250, 3, 40)
     e = [torch.exp(2j * np.pi * torch.remainder(torch.arange(n, device="cuda", dtype=torch.float64) * kk, n) / n)
          for n, kk in zip(shape, k)]
-    x = (e[0][:, None, None, None] * e[1][None, :, None, None]).to(torch.complex64)
-    x = (x[:, :, None, None] * (e[2][:, None] * e[3][None, :]).to(torch.complex64)[None, None]).contiguous()
+    a = (e[0][:, None] * e[1][None, :]).to(torch.complex64)          # [512, 256]
+    b = (e[2][:, None] * e[3][None, :]).to(torch.complex64)          # [128, 64]
+    x = (a[:, :, None, None] * b[None, None, :, :]).contiguous()
+    assert tuple(x.shape) == shape
     f = ndim.FFTN(shape, "c2c", "f32")
     X = f.forward(x)
     torch.cuda.synchronize()
