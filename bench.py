@@ -603,6 +603,24 @@ def batched_workload(afft, torch, steps=10, warmup=3, count=200, seed=200):
 
     ms_single = timed(per_field)
     results = {}
+    # one persistent launch per direction over every field (afft_queue)
+    plans = [afft.Plan((n, n, n), "r2c", "f32", batch=c) for n, c in groups]
+    specs = [torch.empty(p.spectral_shape, dtype=torch.complex64, device="cuda") for p in plans]
+    backs = [torch.empty(p.spatial_shape, dtype=torch.float32, device="cuda") for p in plans]
+    ins = [fields[n] for n, _ in groups]
+    q = afft.Queue(plans)
+
+    def queued():
+        q.forward(ins, specs)
+        q.backward(specs, backs)
+
+    ms_q = timed(queued)
+    err_q = max(float(torch.linalg.vector_norm(b - x) / torch.linalg.vector_norm(x)) for b, x in zip(backs, ins))
+    status_q = q.status()
+    items_q = (q.items(False), q.items(True))
+    q.close()
+    for p in plans:
+        p.close()
     for tuned in (False, True):
         plans = [afft.Plan((n, n, n), "r2c", "f32", batch=c) for n, c in groups]
         if tuned:
@@ -633,8 +651,12 @@ def batched_workload(afft, torch, steps=10, warmup=3, count=200, seed=200):
            "solves_per_s_one_execute_per_field": count / (ms_single * 1e-3),
            "solves_per_s_batched_graph": count / (results["batched"][0] * 1e-3),
            "solves_per_s_batched_graph_tuned": count / (results["tuned"][0] * 1e-3),
+           "solves_per_s_persistent_queue": count / (ms_q * 1e-3),
+           "frac_of_hbm_roofline_persistent_queue": step_bytes / (ms_q * 1e-3) / 1e9 / peaks()[0],
+           "persistent_queue": {"launches_per_step": 2, "work_items": list(items_q), "status": status_q,
+                                "round_trip_rel_l2_max": err_q},
            "ms_per_step": {"one_execute_per_field": ms_single, "batched_graph": results["batched"][0],
-                           "batched_graph_tuned": results["tuned"][0]},
+                           "batched_graph_tuned": results["tuned"][0], "persistent_queue": ms_q},
            "round_trip_rel_l2_max": max(results["batched"][1], results["tuned"][1])}
     out["speedup_batched_tuned_vs_per_field"] = ms_single / results["tuned"][0]
     return out

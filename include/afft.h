@@ -324,6 +324,39 @@ int afft_multi_create(afft_multi **out, int nplans, afft_plan *const *plans);
 int afft_multi_execute(afft_multi *m, int backward, const void *const *in, void *const *out, void *cuda_stream);
 int afft_multi_destroy(afft_multi *m);
 
+/*
+ * Persistent executor: several FP32 r2c plans (typically one batched plan per
+ * distinct size of a set of uneven fields) run as ONE kernel launch per
+ * direction.  This is the GPU form of the paper's batch bookkeeping (Algorithm
+ * 2 repeats the stages per array; Section 3's planner picks kernels per size):
+ * creation lists every tile of every stage (r2c, N1, N0 forward; N0, N1, c2r
+ * backward) of every field as a work item, ordered so that each item comes
+ * after the items it depends on; during the launch each CTA walks its share of
+ * the list and waits, on device counters, for the r2c tiles of a plane before
+ * its N1 tiles and for all N1 tiles of a field before its N0 tiles (backward:
+ * N0 before N1, a plane's N1 before its c2r).  A field's stages thus run close
+ * together in time and its intermediate spectrum is often still in L2.
+ * Supported: r2c, AFFT_F32, all three axes, no four-step axis, line lengths
+ * n0, n1 in {48, 64, 96, 120, 128, 160, 256} and n2/2 in {24, 32, 48, 60, 64,
+ * 80, 128}, at most 8 plans, all on the current device (AFFT_ERR_UNSUPPORTED
+ * otherwise).  Creation allocates the item lists (about 24 bytes per tile) and
+ * the counters and synchronises; the plans stay owned by the caller and must
+ * outlive the executor.  Execution: in[i], out[i] as for afft_execute_forward /
+ * _backward on plans[i] (forward: real in, spectrum out; backward: spectrum in,
+ * not modified, real out, x 1/N), asynchronous on the stream, allocates
+ * nothing; the plans' workspaces are used, so a plan must not run elsewhere
+ * meanwhile, and two executions of one executor must not overlap.  Every wait
+ * on a counter is bounded (about 2 s): a CTA that gives up records it and makes
+ * the others stop early; afft_queue_status (synchronising) then returns
+ * AFFT_ERR_TIMEOUT once, and that execution's outputs are incomplete.
+ */
+typedef struct afft_queue afft_queue;
+int afft_queue_create(afft_queue **out, int nplans, afft_plan *const *plans);
+int afft_queue_execute(afft_queue *q, int backward, const void *const *in, void *const *out, void *cuda_stream);
+int afft_queue_status(afft_queue *q);
+int afft_queue_items(const afft_queue *q, int backward);   /* work items of one direction (0 for NULL) */
+int afft_queue_destroy(afft_queue *q);                    /* NULL is a no-op */
+
 /* Number of kernel launches one execute_forward / execute_backward makes. */
 int afft_plan_launches(const afft_plan *p, int backward);
 

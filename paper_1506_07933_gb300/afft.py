@@ -43,7 +43,8 @@ EXPORTS = [
     "afft_plan_create_batched", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
     "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe",
     "afft_plan_set_blocked", "afft_plan_get_tuning", "afft_plan_set_tuning", "afft_plan_create_axes",
-    "afft_plan_set_backward_scale", "afft_plan_backward_scale", "afft_copy_2d",
+    "afft_plan_set_backward_scale", "afft_plan_backward_scale", "afft_copy_2d", "afft_queue_create",
+    "afft_queue_execute", "afft_queue_status", "afft_queue_items", "afft_queue_destroy",
 ]
 
 _lib = None
@@ -72,6 +73,11 @@ def load(path: str = None):
     lib.afft_plan_backward_scale.argtypes = [vp]
     lib.afft_plan_backward_scale.restype = ctypes.c_double
     lib.afft_copy_2d.argtypes = [vp, sz, vp, sz, sz, sz, vp]
+    lib.afft_queue_create.argtypes = [ctypes.POINTER(vp), c_int, ctypes.POINTER(vp)]
+    lib.afft_queue_execute.argtypes = [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.afft_queue_status.argtypes = [vp]
+    lib.afft_queue_items.argtypes = [vp, c_int]
+    lib.afft_queue_destroy.argtypes = [vp]
     lib.afft_plan_tune.argtypes = [vp, vp]
     lib.afft_execute_poisson.argtypes = [vp, vp, vp, vp]
     lib.afft_plan_describe.argtypes = [vp, ctypes.c_char_p, sz]
@@ -108,7 +114,8 @@ def load(path: str = None):
               "afft_plan_set_l2_chunk", "afft_plan_tune", "afft_plan_describe", "afft_multi_create",
               "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe",
               "afft_plan_set_blocked", "afft_plan_get_tuning", "afft_plan_set_tuning", "afft_plan_create_axes",
-              "afft_plan_set_backward_scale", "afft_copy_2d"):
+              "afft_plan_set_backward_scale", "afft_copy_2d", "afft_queue_create", "afft_queue_execute",
+              "afft_queue_status", "afft_queue_items", "afft_queue_destroy"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -441,6 +448,52 @@ class Multi:
         if getattr(self, "_m", None) and self._m.value:
             _check(load().afft_multi_destroy(self._m), "afft_multi_destroy")
             self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Queue:
+    """Several FP32 r2c plans (one batched plan per size) run as one persistent kernel launch per
+    direction (see afft_queue_* in include/afft.h)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._p.value for p in self.plans])
+        self._q = ctypes.c_void_p()
+        _check(load().afft_queue_create(ctypes.byref(self._q), len(self.plans), arr), "afft_queue_create")
+
+    def _run(self, backward, ins, outs, stream):
+        n = len(self.plans)
+        for p, x, y in zip(self.plans, ins, outs):
+            a, b = (p.spectral_shape, p.spatial_shape) if backward else (p.spatial_shape, p.spectral_shape)
+            da, db = (p.spectral_dtype, p.spatial_dtype) if backward else (p.spatial_dtype, p.spectral_dtype)
+            p._check_tensor(x, a, da, "input")
+            p._check_tensor(y, b, db, "output")
+        i = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ins])
+        o = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
+        _check(load().afft_queue_execute(self._q, int(backward), i, o, _stream_handle(stream)), "afft_queue_execute")
+
+    def forward(self, ins, outs, stream=None):
+        self._run(False, ins, outs, stream)
+
+    def backward(self, ins, outs, stream=None):
+        self._run(True, ins, outs, stream)
+
+    def status(self) -> int:
+        """Synchronises; 0, or 11 (AFFT_ERR_TIMEOUT) if a bounded wait ran out since the last call."""
+        return int(load().afft_queue_status(self._q))
+
+    def items(self, backward=False) -> int:
+        return int(load().afft_queue_items(self._q, int(bool(backward))))
+
+    def close(self):
+        if getattr(self, "_q", None):
+            _check(load().afft_queue_destroy(self._q), "afft_queue_destroy")
+            self._q = None
 
     def __del__(self):
         try:

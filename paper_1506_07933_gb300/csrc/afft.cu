@@ -1133,6 +1133,30 @@ bool reshape_contig(afft_plan *p, int target)
 
 }  // namespace
 
+bool afft::plan_view(const afft_plan *p, PlanView *v)
+{
+    if (!p || !v) return false;
+    for (int a = 0; a < 3; ++a) {
+        v->n[a] = p->n[a];
+        v->tw_base[a] = p->ax[a].tw_base;
+        v->line_n[a] = p->ax[a].desc.n;
+        v->specialised[a] = !p->ax[a].ks->generic;
+        v->npass[a] = p->ax[a].desc.npass;
+        for (int i = 0; i < kMaxPasses; ++i) v->radix[a][i] = p->ax[a].desc.radix[i];
+    }
+    v->batch = p->batch;
+    v->nh = p->nh;
+    v->kind = p->kind;
+    v->precision = p->precision;
+    v->axes = p->axes;
+    v->tw = p->d_tw;
+    v->four_step = p->four[0].on || p->four[1].on || p->four[2].on;
+    v->post_off = p->post_off;
+    v->work = p->d_work;
+    v->device = p->device;
+    return true;
+}
+
 // ================================================================== C ABI ===
 
 extern "C" {

@@ -14,6 +14,8 @@
 
 #include <cuda_runtime.h>
 
+struct afft_plan;
+
 namespace afft {
 
 constexpr int kMaxPasses = 16;
@@ -144,6 +146,23 @@ const KernelSet *generic_kernels_f64();
 // an mbarrier that nothing completes, then sets *err.
 cudaError_t launch_wait_probe(unsigned *err, unsigned long long limit_ns, cudaStream_t stream);
 const KernelSet *generic_kernels_split();
+
+// What the persistent multi-plan executor (queue.cu) reads from a plan.
+struct PlanView {
+    long long n[3], batch, nh;
+    int kind, precision, axes;
+    const void *tw;            // twiddle tables (complex of the plan's precision)
+    int tw_base[3];            // first twiddle of each axis' tables
+    int line_n[3];             // line length of each axis' stages (n0, n1, n2 or n2/2)
+    bool specialised[3];       // the axis runs a specialised (compile-time radix) family
+    int radix[3][kMaxPasses];  // that family's radix sequence (npass entries)
+    int npass[3];
+    bool four_step;            // some axis is split four-step
+    int post_off;              // r2c: first entry of the w_{n2}^k table
+    void *work;                // r2c workspace (n0 n1 nh complex per transform)
+    int device;
+};
+bool plan_view(const afft_plan *p, PlanView *v);
 const KernelSet *spec_kernels_split(int n);
 constexpr size_t kSplitTableBytes = 2 * 32 * 32 * sizeof(unsigned);
 cudaError_t split_fragments(unsigned *table, cudaStream_t stream);

@@ -74,17 +74,24 @@ template <typename V> struct SmemLines {
 
 // Global accessors store type V and compute in CT (the same, or float-float
 // for FP64 data): sources convert on load and record out-of-range values in
-// *bad, sinks convert on store.
+// *bad, sinks convert on store.  CG sources load through L2 only (ld.global.cg):
+// the persistent executor reads data that other CTAs of the same launch wrote,
+// which a copy cached in L1 (or read through the non-coherent path) could miss.
+template <bool CG, typename V> __device__ __forceinline__ V ld_data(const V *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
 
 // Global columns c0 .. c0+lines-1 of a [outer][n][W] slab (strided stage).
-template <typename V, typename CT = V> struct GlobalCols {
+template <typename V, typename CT = V, bool CG = false> struct GlobalCols {
     const V *base;                 // &x[o][0][c0]
     long long W;
     int valid;                     // columns of the tile inside the array
     DfFlags *bad;
     __device__ __forceinline__ CT operator()(int l, int p) const
     {
-        return l < valid ? Conv<CT, V>::in(base[(long long)p * W + l], bad) : czero<CT>();
+        return l < valid ? Conv<CT, V>::in(ld_data<CG>(base + (long long)p * W + l), bad) : czero<CT>();
     }
 };
 template <typename V, typename CT = V> struct GlobalColsOut {
@@ -146,7 +153,7 @@ template <typename V, typename CT = V> struct GlobalLinesOut {
 //   E[k] = X[k] + conj(X[M-k]),  O[k] = (X[k] - conj(X[M-k])) w_{2M}^{+k},
 // with the imaginary parts of the self-conjugate bins X[0], X[M] dropped.
 // (The factor 1/2 of the textbook identity is folded into the 1/N scale.)
-template <typename V, typename CT = V> struct C2RPre {
+template <typename V, typename CT = V, bool CG = false> struct C2RPre {
     const V *base;                 // &X[b0][0]
     const CT *post_tw;             // w_{2M}^k forward, k = 0..M
     int M;
@@ -157,8 +164,8 @@ template <typename V, typename CT = V> struct C2RPre {
     {
         if (l >= valid) return czero<CT>();
         const V *x = base + l * ld;
-        CT a = Conv<CT, V>::in(x[k], bad);
-        CT b = cconj(Conv<CT, V>::in(x[M - k], bad));
+        CT a = Conv<CT, V>::in(ld_data<CG>(x + k), bad);
+        CT b = cconj(Conv<CT, V>::in(ld_data<CG>(x + M - k), bad));
         if (k == 0) {
             a.y = typename RealOf<CT>::T();
             b.y = typename RealOf<CT>::T();
