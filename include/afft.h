@@ -278,8 +278,9 @@ size_t afft_plan_l2_chunk(const afft_plan *p);
  * round trips of this plan on temporary buffers (allocated and freed here,
  * filled by afft_fill_uniform) for: the points per CTA of the contiguous
  * stage (1024 .. 8192), pipelined or plain kernels for each strided stage,
- * and, for arrays beyond 192 MB, the L2 slab size (0, 32, 64 MB); keeps the
- * fastest choice of each, in that order.  Results do not depend on the choice
+ * early release of the load buffer for row-pair tiles (odd-width complex64
+ * rows), and, for arrays beyond 192 MB, the L2 slab size (0, 32, 64 MB); keeps
+ * the fastest choice of each, in that order.  Results do not depend on the choice
  * beyond rounding.  Synchronises the stream.  AFFT_ERR_NOMEM if the temporary
  * buffers do not fit.
  */
@@ -290,13 +291,14 @@ int afft_plan_tune(afft_plan *p, void *cuda_stream);
  * them in a cache file keyed by shape, kind, precision, batch and GPU):
  * cfg[0] points per CTA of the contiguous stage (0: the default), cfg[1] and
  * cfg[2] pipelined (1) or plain (0) kernels for the N0 and N1 stages, cfg[3]
- * the L2 slab size in bytes (0: unfused).  set returns AFFT_ERR_UNSUPPORTED
- * for a pipelined stage or a CTA size this plan cannot use, AFFT_ERR_SIZE for
- * a negative value; it allocates nothing on the device.  Not while the plan
- * is in use on a stream.
+ * the L2 slab size in bytes (0: unfused), cfg[4] and cfg[5] whether the N0 and
+ * N1 stages' row-pair tiles (odd-width complex64 rows) release their load
+ * buffer after the first pass.  set returns AFFT_ERR_UNSUPPORTED for a choice
+ * this plan cannot use, AFFT_ERR_SIZE for a negative value; it allocates
+ * nothing on the device.  Not while the plan is in use on a stream.
  */
-int afft_plan_get_tuning(const afft_plan *p, int64_t cfg[4]);
-int afft_plan_set_tuning(afft_plan *p, const int64_t cfg[4]);
+int afft_plan_get_tuning(const afft_plan *p, int64_t cfg[6]);
+int afft_plan_set_tuning(afft_plan *p, const int64_t cfg[6]);
 
 /*
  * Writes a one-line JSON description of the plan's configuration (radix

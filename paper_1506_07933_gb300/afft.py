@@ -359,13 +359,16 @@ class Plan:
 
     @property
     def tuning(self) -> list:
-        """[contiguous-stage points per CTA (0: default), N0 pipelined, N1 pipelined, L2 slab bytes]."""
-        cfg = (ctypes.c_int64 * 4)()
+        """[contiguous-stage points per CTA (0: default), N0 pipelined, N1 pipelined, L2 slab bytes,
+        N0 row-pair early release, N1 row-pair early release]."""
+        cfg = (ctypes.c_int64 * 6)()
         _check(load().afft_plan_get_tuning(self._p, cfg), "afft_plan_get_tuning")
         return [int(v) for v in cfg]
 
     def set_tuning(self, cfg) -> None:
-        arr = (ctypes.c_int64 * 4)(*[int(v) for v in cfg])
+        """Applies a tuning list (a 4-entry list from an older cache leaves the row-pair choices off)."""
+        cfg = [int(v) for v in cfg] + [0] * (6 - len(cfg))
+        arr = (ctypes.c_int64 * 6)(*cfg[:6])
         _check(load().afft_plan_set_tuning(self._p, arr), "afft_plan_set_tuning")
 
     def describe(self) -> dict:
@@ -518,9 +521,9 @@ def tuning_cache_lookup(path: str, key: str):
             cfg = json.load(fh).get(key)
     except (OSError, ValueError, AttributeError):
         return None
-    if not isinstance(cfg, list) or len(cfg) != 4 or not all(isinstance(v, int) for v in cfg):
+    if not isinstance(cfg, list) or len(cfg) not in (4, 6) or not all(isinstance(v, int) for v in cfg):
         return None
-    return cfg
+    return cfg + [0] * (6 - len(cfg))   # entries stored before the row-pair choices existed
 
 
 def tuning_cache_store(path: str, key: str, cfg) -> None:

@@ -38,6 +38,7 @@ struct AxisPlan {
     bool pipe;             // in use (the autotuner may switch it off)
     int pipe_slots;        // CTAs resident at once (SMs x CTAs per SM): the persistent grid's cap
     int rp_slots;          // the same for the row-pair kernel of odd-width rows (0: none)
+    bool rp_early;         // row-pair tiles release their load buffer after the first pass (tunable)
 };
 
 // Four-step split of one axis whose lines are longer than a CTA holds
@@ -386,15 +387,23 @@ int plan_shapes(afft_plan *p)
         ap.pipe_avail = !far;
         ap.pipe = !far;
         ap.rp_slots = 0;
+        ap.rp_early = false;
         if (ks->pipe_rp[0] && ks->pipe_smem_rp <= max_smem) {
             bool ok = true;
             for (int k = 0; k < 2 && ok; ++k)
                 ok = cudaFuncSetAttribute(ks->pipe_rp[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          ks->pipe_smem_rp) == cudaSuccess;
+                                          ks->pipe_smem_rp) == cudaSuccess &&
+                     (!ks->pipe_rp_early[k] ||
+                      cudaFuncSetAttribute(ks->pipe_rp_early[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           ks->pipe_smem_rp) == cudaSuccess);
             int rs = 0;
             if (ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rs, ks->pipe_rp[0], ks->pipe_threads,
                                                                     ks->pipe_smem_rp) == cudaSuccess && rs >= 1)
                 ap.rp_slots = sms * rs;
+            // early release by default when the first pass works on column pairs (radix <= 8):
+            // measured on 512-point N1 stages 0.207 -> 0.201 ms, while a radix-16 first pass
+            // (384 = 16 x 8 x 3) measured 0.100 -> 0.112 ms; the autotuner tries both
+            ap.rp_early = ap.rp_slots > 0 && ks->pipe_rp_early[0] && ks->radix[0] <= 8;
             cudaGetLastError();
         }
     }
@@ -584,8 +593,9 @@ cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, lo
         const unsigned grid = (unsigned)std::min<long long>(nt, a.rp_slots);
         void *args[] = {(void *)&in, (void *)&out, (void *)&map, (void *)&tw,   (void *)&W,
                         (void *)&tpo, (void *)&nt, (void *)&err, (void *)&twdf, (void *)&mma};
-        return cudaLaunchKernel(a.ks->pipe_rp[backward ? 1 : 0], dim3(grid), dim3(a.ks->pipe_threads), args,
-                                (size_t)a.ks->pipe_smem_rp, s);
+        const void *fn = a.rp_early && a.ks->pipe_rp_early[0] ? a.ks->pipe_rp_early[backward ? 1 : 0]
+                                                              : a.ks->pipe_rp[backward ? 1 : 0];
+        return cudaLaunchKernel(fn, dim3(grid), dim3(a.ks->pipe_threads), args, (size_t)a.ks->pipe_smem_rp, s);
     }
     const bool tma = encode_strided_map(&map, in, outer, a.desc.n, W, sizeof(V), a.ks->pipe_lines);
     return pipe_on_map<V>(a, map, tma, in, out, tw, outer, W, backward, err, 0, 0, s);
@@ -1559,6 +1569,16 @@ int afft_plan_tune(afft_plan *p, void *stream)
             const float without = measure();
             ap.pipe = !(without > 0 && (with < 0 || without < with));
         }
+        // 2b. row-pair tiles (odd-width complex64 rows): early release of the load buffer or not
+        for (int a = 1; a >= 0; --a) {
+            AxisPlan &ap = p->ax[a];
+            if (!ap.pipe || ap.rp_slots <= 0 || !ap.ks->pipe_rp_early[0]) continue;
+            ap.rp_early = false;
+            const float plain = measure();
+            ap.rp_early = true;
+            const float early = measure();
+            ap.rp_early = early > 0 && (plain < 0 || early < plain);
+        }
         // 3. L2 slab schedule for arrays well beyond L2
         const size_t array = (size_t)p->batch * p->n[0] * p->n[1] * p->nh * c;
         if (array > ((size_t)192 << 20)) {
@@ -1583,28 +1603,35 @@ int afft_plan_tune(afft_plan *p, void *stream)
     return st;
 }
 
-int afft_plan_get_tuning(const afft_plan *p, int64_t cfg[4])
+int afft_plan_get_tuning(const afft_plan *p, int64_t cfg[6])
 {
     if (!p || !cfg) return AFFT_ERR_NULL;
     cfg[0] = p->contig_target;
     cfg[1] = p->ax[0].pipe;
     cfg[2] = p->ax[1].pipe;
     cfg[3] = (int64_t)p->chunk_bytes;
+    cfg[4] = p->ax[0].rp_early;
+    cfg[5] = p->ax[1].rp_early;
     return AFFT_OK;
 }
 
-int afft_plan_set_tuning(afft_plan *p, const int64_t cfg[4])
+int afft_plan_set_tuning(afft_plan *p, const int64_t cfg[6])
 {
     if (!p || !cfg) return AFFT_ERR_NULL;
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a) {
         if (cfg[1 + a] && !p->ax[a].pipe_avail) return AFFT_ERR_UNSUPPORTED;
-    if (cfg[0] < 0 || cfg[3] < 0) return AFFT_ERR_SIZE;
+        if (cfg[4 + a] && (p->ax[a].rp_slots <= 0 || !p->ax[a].ks->pipe_rp_early[0])) return AFFT_ERR_UNSUPPORTED;
+    }
+    if (cfg[0] < 0 || cfg[3] < 0 || cfg[4] < 0 || cfg[5] < 0) return AFFT_ERR_SIZE;
     if (!p->four[2].on) {
         const bool ok = p->precision == AFFT_F64 ? reshape_contig<double2>(p, (int)cfg[0])
                                                  : reshape_contig<float2>(p, (int)cfg[0]);
         if (!ok) return AFFT_ERR_UNSUPPORTED;
     }
-    for (int a = 0; a < 2; ++a) p->ax[a].pipe = cfg[1 + a] != 0;
+    for (int a = 0; a < 2; ++a) {
+        p->ax[a].pipe = cfg[1 + a] != 0;
+        p->ax[a].rp_early = cfg[4 + a] != 0;
+    }
     return configure_chunks(p, (size_t)cfg[3]);
 }
 
@@ -1650,6 +1677,7 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         "\"radix\": [\"%s\", \"%s\", \"%s\"], \"specialised\": [%d, %d, %d], \"four_step\": [%d, %d, %d], "
         "\"pipelined\": [%d, %d], \"contig_lines\": %d, \"strided_lines\": [%d, %d], "
         "\"l2_slab_planes\": %d, \"blocked\": %d, \"axes\": %d, \"backward_scale\": %.17g, "
+        "\"rp_early\": [%d, %d], "
         "\"stage_kernels_forward\": [\"%s\", \"%s\", \"%s\"], \"stage_kernels_backward\": [\"%s\", \"%s\", \"%s\"]}",
         (long long)p->n[0], (long long)p->n[1], (long long)p->n[2], (long long)p->batch,
         p->kind == AFFT_C2C ? "c2c" : "r2c",
@@ -1658,6 +1686,7 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         p->four[2].on, p->ax[0].pipe, p->ax[1].pipe, p->ax[2].launch.lines,
         p->ax[0].pipe ? p->ax[0].ks->pipe_lines : p->ax[0].launch.lines,
         p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, p->chunk_planes, (int)blk, p->axes, p->bscale,
+        (int)p->ax[0].rp_early, (int)p->ax[1].rp_early,
         blk ? "k_contig" : zf, y, x, x, y, blk ? "k_contig" : zb);
     if (need < 0) return AFFT_ERR_CUDA;
     return (size_t)need < len ? AFFT_OK : AFFT_ERR_SIZE;

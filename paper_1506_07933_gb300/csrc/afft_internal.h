@@ -130,6 +130,7 @@ struct KernelSet {
     // through TMA ([0] forward, [1] backward; the first ten arguments of pipe[], see
     // k_strided_pipe_rp) and their shared memory; null / 0 elsewhere
     const void *pipe_rp[2];
+    const void *pipe_rp_early[2];  // the same with the load buffer released after the first pass
     int pipe_smem_rp;
 };
 

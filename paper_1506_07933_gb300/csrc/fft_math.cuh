@@ -301,6 +301,14 @@ template <> __device__ __forceinline__ dcx ldgc<dcx>(const dcx *p)
     return r;
 }
 
+// A twiddle factor: from a table in shared memory (a CTA's staged copy) or,
+// through the read-only cache, from the plan's table in global memory.
+template <bool Smem, typename V> __device__ __forceinline__ V tw_ld(const V *p)
+{
+    if constexpr (Smem) return *p;
+    else return ldgc(p);
+}
+
 // Storage <-> compute conversions (identity unless double2 <-> dcx).
 template <typename CT, typename V> struct Conv {
     static __device__ __forceinline__ CT in(V v, DfFlags *) { return v; }

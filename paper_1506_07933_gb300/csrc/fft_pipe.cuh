@@ -159,12 +159,24 @@ template <class P, typename V> struct PipeShape {
     using seq = typename P::seq;
     static constexpr int npass = P::npass;
     static constexpr int tile = P::n * lines;                       // complex elements per tile
-    static constexpr int smem = 3 * tile * (int)sizeof(V) + 16;     // 3 buffers, then two mbarriers
+    // twiddle entries of the line's passes (Ns (R - 1) per pass with Ns > 1, in pass order)
+    template <int... Rs> __host__ __device__ static constexpr int tw_count(Seq<Rs...>)
+    {
+        int ns = 1, c = 0;
+        for (int r : {Rs...}) {
+            if (ns > 1) c += ns * (r - 1);
+            ns *= r;
+        }
+        return c;
+    }
+    // complex64 tiles stage the table in shared memory (behind the mbarriers), once per CTA
+    static constexpr int tw_smem = sizeof(V) == 8 ? tw_count(seq{}) : 0;
+    static constexpr int smem = 3 * tile * (int)sizeof(V) + 16 + tw_smem * 8;   // 3 buffers, mbarriers, table
     // odd-width complex64 rows read as row pairs (k_strided_pipe_rp): load buffers of two
     // [n/2][lines + 2] boxes, then the scratch tile and the mbarriers
     static constexpr int lw = lines + 2;
     static constexpr int tile_rp = P::n * lw;
-    static constexpr int smem_rp = (2 * tile_rp + tile) * (int)sizeof(V) + 16;
+    static constexpr int smem_rp = (2 * tile_rp + tile) * (int)sizeof(V) + 16 + tw_smem * 8;
     static constexpr bool rp_ok = sizeof(V) == 8 && lines == 16 && P::n % 16 == 0 && P::n / 2 <= 256;
     static constexpr int box_rows = tma_box_rows(P::n);
     static_assert((box_rows * lines * (int)sizeof(V)) % 128 == 0 || box_rows == P::n,
@@ -202,7 +214,7 @@ struct PairGlobalOut {
 // butterflies are (column pair lp, butterfly j), reading both columns' R
 // values with 16-byte loads and sharing the twiddles.  InPlace: every read of
 // the CTA precedes a barrier, every write follows it (src and dst may alias).
-template <int R, int S, int N, int Ns, int LG, int NT, int B, bool InPlace = false, class Dst>
+template <int R, int S, int N, int Ns, int LG, int NT, int B, bool InPlace = false, bool TwSmem = false, class Dst>
 __device__ __forceinline__ void pair_pass(const float2 *src, const float2 *__restrict__ tw, const Dst &dst)
 {
     constexpr int PAIRS = (1 << LG) / 2, NB = N / R, TOTAL = PAIRS * NB;
@@ -224,7 +236,7 @@ __device__ __forceinline__ void pair_pass(const float2 *src, const float2 *__res
                 const float2 *t = tw + k * (R - 1);
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const float2 w = ldgc(t + r - 1);
+                    const float2 w = tw_ld<TwSmem>(t + r - 1);
                     lo[b][r] = ctw<S>(lo[b][r], w);
                     hi[b][r] = ctw<S>(hi[b][r], w);
                 }
@@ -271,8 +283,8 @@ template <typename V, typename CT = V> struct TileOut {
 // and writes the other one; the last pass writes the stage's output.  Split:
 // radix-16 passes of complex64 tiles on the tensor cores (fft_split.cuh, table
 // `mma` of both directions).
-template <class Sh, int S, int N, int Ns, int TwOff, int Q, bool Split = false, typename V, class Out, int R,
-          int... Rest>
+template <class Sh, int S, int N, int Ns, int TwOff, int Q, bool Split = false, bool TwSmem = false, typename V,
+          class Out, int R, int... Rest>
 __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V *tw, const Out &out,
                                             const unsigned *mma = nullptr)
 {
@@ -282,14 +294,19 @@ __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V
     V *dst = (Q % 2 == 0) ? C : X;
     if constexpr (Sh::pairs(R)) {
         constexpr int B = Sh::per_thread(R);
-        if constexpr (Last) pair_pass<R, S, N, Ns, LG, NT, B>(src, tw + TwOff, out.pair);
-        else pair_pass<R, S, N, Ns, LG, NT, B>(src, tw + TwOff, PairSmemOut<LG>{dst});
+        if constexpr (Last) pair_pass<R, S, N, Ns, LG, NT, B, false, TwSmem>(src, tw + TwOff, out.pair);
+        else pair_pass<R, S, N, Ns, LG, NT, B, false, TwSmem>(src, tw + TwOff, PairSmemOut<LG>{dst});
     } else {
         const SmemRowsC<V, LG> in_rows{src};
         constexpr int B = Sh::per_thread(R);
         if constexpr (Last && Split && R == 16)
             spec_pass<R, S, false, Split, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
                                                  out.cols, mma);
+        else if constexpr (Last && TwSmem)
+            radix_pass<R, S, false, NT, B, true>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows, out.single);
+        else if constexpr (TwSmem)
+            radix_pass<R, S, false, NT, B, true>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                                 SmemRowsC<V, LG>{dst});
         else if constexpr (Last)
             spec_pass<R, S, false, Split, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
                                                  out.single, mma);
@@ -300,7 +317,7 @@ __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V
     if constexpr (!Last) {
         __syncthreads();
         constexpr int next = TwOff + (Ns > 1 ? Ns * (R - 1) : 0);
-        pipe_passes<Sh, S, N, Ns * R, next, Q + 1, Split>(Seq<Rest...>{}, X, C, tw, out, mma);
+        pipe_passes<Sh, S, N, Ns * R, next, Q + 1, Split, TwSmem>(Seq<Rest...>{}, X, C, tw, out, mma);
     }
 }
 
@@ -313,12 +330,13 @@ __device__ __forceinline__ void scratch_passes(Seq<R, Rest...>, float2 *C, const
     constexpr bool Global = sizeof...(Rest) == 0;
     constexpr int LG = Sh::lg, NT = Sh::threads, B = Sh::covering(R);
     if constexpr (Sh::pairs(R)) {
-        if constexpr (Global) pair_pass<R, S, N, Ns, LG, NT, B>(C, tw + TwOff, out.pair);
-        else pair_pass<R, S, N, Ns, LG, NT, B, true>(C, tw + TwOff, PairSmemOut<LG>{C});
+        if constexpr (Global) pair_pass<R, S, N, Ns, LG, NT, B, false, true>(C, tw + TwOff, out.pair);
+        else pair_pass<R, S, N, Ns, LG, NT, B, true, true>(C, tw + TwOff, PairSmemOut<LG>{C});
     } else {
         const SmemRowsC<float2, LG> rows{C};
-        if constexpr (Global) radix_pass<R, S, false, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, rows, out.single);
-        else radix_pass<R, S, true, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, rows, rows);
+        if constexpr (Global)
+            radix_pass<R, S, false, NT, B, true>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, rows, out.single);
+        else radix_pass<R, S, true, NT, B, true>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, rows, rows);
     }
     if constexpr (sizeof...(Rest) > 0) {
         __syncthreads();
@@ -381,6 +399,16 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
 
     long long t = blockIdx.x;
     if (t >= ntiles) return;
+    // Complex64 TMA tiles of two or more passes release their load buffer after
+    // the first pass, so two loads are in flight while the rest runs; otherwise
+    // the next tile's load is issued once this one has landed.
+    constexpr bool Early = TMA && !Split && sizeof(V) == 8 && P::npass >= 2;
+    // those tiles read their twiddles from a copy of the line's table in shared memory, staged
+    // once per CTA (the factors of a pass are the same for every tile)
+    float2 *const tw_s = reinterpret_cast<float2 *>(pipe_smem_raw + 3 * TILE_BYTES + 16);
+    if constexpr (Early) {
+        for (int e = tid; e < Sh::tw_smem; e += NT) tw_s[e] = ldgc(reinterpret_cast<const float2 *>(tw) + e);
+    }
     if (TMA && tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -422,10 +450,6 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
         }
     };
     auto out_col = [&](long long c) -> long long { return c < W ? c : -1; };
-    // Complex64 TMA tiles of two or more passes release their load buffer after
-    // the first pass, so two loads are in flight while the rest runs; otherwise
-    // the next tile's load is issued once this one has landed.
-    constexpr bool Early = TMA && !Split && sizeof(V) == 8 && P::npass >= 2;
 
     issue(t, 0);
     if (Early && t + gridDim.x < ntiles) issue(t + gridDim.x, 1);
@@ -472,8 +496,7 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
         }
         if constexpr (Early) {
             const float2 *x = reinterpret_cast<const float2 *>(buf0 + b * TILE);
-            early_release_passes<Sh, S, N>(typename P::seq{}, x, reinterpret_cast<float2 *>(scratch),
-                                           reinterpret_cast<const float2 *>(tw), to, [&] {
+            early_release_passes<Sh, S, N>(typename P::seq{}, x, reinterpret_cast<float2 *>(scratch), tw_s, to, [&] {
                                                if (tn + gridDim.x < ntiles) issue(tn + gridDim.x, b);
                                            });
         } else if (!done) {
@@ -578,14 +601,35 @@ __device__ __forceinline__ void rp_passes(Seq<R0, Rest...>, float2 *X, float2 *C
     }
     if constexpr (!Last) {
         __syncthreads();
-        pipe_passes<Sh, S, N, R0, 0, 1>(Seq<Rest...>{}, X, C, tw, out);
+        pipe_passes<Sh, S, N, R0, 0, 1, false, true>(Seq<Rest...>{}, X, C, tw, out);
     }
+}
+
+// Early release for row-pair tiles: the first pass reads the boxes (X -> C), then
+// `released` issues the load of the tile after next into X while the other
+// passes run in place on C.
+template <class Sh, int S, int N, class Out, class Released, int R0, int... Rest>
+__device__ __forceinline__ void rp_early_passes(Seq<R0, Rest...>, const float2 *X, float2 *C, const float2 *tw,
+                                                const Out &out, int l, const Released &released)
+{
+    static_assert(sizeof...(Rest) >= 1, "the first pass must not be the last");
+    constexpr int LG = Sh::lg, NT = Sh::threads, LW = Sh::lw;
+    const float2 *A = X, *Bx = X + (N / 2) * LW;
+    if constexpr (Sh::pairs(R0))
+        pair_pass_rp<R0, S, N, LW, LG, NT, Sh::per_thread(R0)>(A, Bx, PairSmemOut<LG>{C});
+    else
+        radix_pass<R0, S, false, NT, Sh::per_thread(R0)>(N, 1, tw, Sh::lines, MapLineFastC<LG>{}, RowPairIn<LW>{A, Bx, l},
+                                                        SmemRowsC<float2, LG>{C});
+    __syncthreads();
+    released();
+    scratch_passes<Sh, S, N, R0, 0>(Seq<Rest...>{}, C, tw, out);
 }
 
 // Persistent, double-buffered strided stage over odd-width complex64 rows (same
 // argument list as k_strided_pipe; the tensor map views [outer][n/2][2W] with
-// boxes of 18 x n/2).
-template <class P, int S>
+// boxes of 18 x n/2).  Early: the load buffer is released after the first pass
+// (two tile loads in flight during the other passes), as k_strided_pipe does.
+template <class P, int S, bool Early = false>
 __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
     k_strided_pipe_rp(const float2 *__restrict__, float2 *out, const __grid_constant__ CUtensorMap tmap,
                       const float2 *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
@@ -601,10 +645,13 @@ __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
     V *const scratch = buf0 + 2 * TILE_RP;
     unsigned long long *const bars =
         reinterpret_cast<unsigned long long *>(pipe_smem_raw + (2 * TILE_RP + Sh::tile) * sizeof(V));
+    // the line's twiddle table, staged once per CTA behind the mbarriers
+    float2 *const tw_s = reinterpret_cast<float2 *>(pipe_smem_raw + (2 * TILE_RP + Sh::tile) * sizeof(V) + 16);
     const int tid = threadIdx.x;
 
     long long t = blockIdx.x;
     if (t >= ntiles) return;
+    for (int e = tid; e < Sh::tw_smem; e += Sh::threads) tw_s[e] = ldgc(tw + e);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -622,18 +669,22 @@ __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
         tma_load_3d(buf0 + b * TILE_RP + (N / 2) * LW, &tmap, (int)(W + c0 - 1), 0, (int)o, &bars[b]);
     };
 
-    // The next tile's load is issued once this one has landed (the load buffer is not released
-    // after the first pass as in k_strided_pipe: that measured 3-5% slower on 512-point stages).
+    // Without Early the next tile's load is issued once this one has landed.
     issue(t, 0);
+    if (Early && t + gridDim.x < ntiles) issue(t + gridDim.x, 1);
     for (int i = 0;; ++i) {
         const int b = i & 1;
+        const long long tn = t + gridDim.x;
         const bool ok = mbar_wait_bounded(&bars[b], (unsigned)((i >> 1) & 1));
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(err, 1u);
+            if (tid == 0) {
+                atomicExch(err, 1u);
+                // the other buffer's load, if one was issued, must land before the CTA exits
+                if (Early && tn < ntiles) mbar_wait_bounded(&bars[b ^ 1], (unsigned)(((i + 1) >> 1) & 1));
+            }
             return;
         }
-        const long long tn = t + gridDim.x;
-        if (tn < ntiles) issue(tn, b ^ 1);
+        if (!Early && tn < ntiles) issue(tn, b ^ 1);
 
         const long long o = t / tiles_per_outer;
         const long long c0 = (t - o * tiles_per_outer) * LINES;
@@ -644,7 +695,12 @@ __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
         to.single = GlobalColFixedOut<V>{obase, W, c0 + l < W ? c0 + l : -1};
         to.pair = PairGlobalOutOdd{obase, W, a < W ? a : -1, a + 1 < W ? a + 1 : -1,
                                    a + 1 < W && (reinterpret_cast<unsigned long long>(obase) & 15) == 0};
-        rp_passes<Sh, S, N>(typename P::seq{}, buf0 + b * TILE_RP, scratch, tw, to, l);
+        if constexpr (Early && P::npass >= 2)
+            rp_early_passes<Sh, S, N>(typename P::seq{}, buf0 + b * TILE_RP, scratch, tw_s, to, l, [&] {
+                if (tn + gridDim.x < ntiles) issue(tn + gridDim.x, b);
+            });
+        else
+            rp_passes<Sh, S, N>(typename P::seq{}, buf0 + b * TILE_RP, scratch, tw_s, to, l);
         if (tn >= ntiles) break;
         t = tn;
     }
@@ -854,6 +910,10 @@ template <class F, typename V> KernelSet kernel_set(int n, int npass, const int 
             if constexpr (Sh::rp_ok && !F::split) {
                 k.pipe_rp[0] = (const void *)k_strided_pipe_rp<P, -1>;
                 k.pipe_rp[1] = (const void *)k_strided_pipe_rp<P, +1>;
+                if constexpr (P::npass >= 2) {
+                    k.pipe_rp_early[0] = (const void *)k_strided_pipe_rp<P, -1, true>;
+                    k.pipe_rp_early[1] = (const void *)k_strided_pipe_rp<P, +1, true>;
+                }
                 k.pipe_smem_rp = Sh::smem_rp;
             }
         }

@@ -58,7 +58,8 @@ struct MapButterflyFast {  // contiguous stage: consecutive threads walk along a
 // InPlace the pass reads everything into registers, waits for the whole CTA,
 // then writes.
 
-template <int R, int S, bool InPlace, int NT = 0, int BM = 0, typename V, class Map, class Src, class Dst>
+template <int R, int S, bool InPlace, int NT = 0, int BM = 0, bool TwSmem = false, typename V, class Map, class Src,
+          class Dst>
 __device__ __forceinline__ void radix_pass(int n, int Ns, const V *__restrict__ tw, int lines,
                                            const Map &map, const Src &src, const Dst &dst)
 {
@@ -83,7 +84,7 @@ __device__ __forceinline__ void radix_pass(int n, int Ns, const V *__restrict__ 
             if (Ns > 1) {
                 const V *t = tw + (j % Ns) * (R - 1);
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[b][r] = ctw<S>(v[b][r], ldgc(t + r - 1));
+                for (int r = 1; r < R; ++r) v[b][r] = ctw<S>(v[b][r], tw_ld<TwSmem>(t + r - 1));
             }
             Dft<R, S, V>::run(v[b]);
         }

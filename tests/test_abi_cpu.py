@@ -102,7 +102,7 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
 
 
 def test_tuning_calls_reject_null(lib):
-    cfg = (ctypes.c_int64 * 4)()
+    cfg = (ctypes.c_int64 * 6)()
     assert lib.afft_plan_get_tuning(None, cfg) == 1
     assert lib.afft_plan_set_tuning(None, cfg) == 1
     assert lib.afft_plan_set_blocked(None, 1) == 1
@@ -118,20 +118,20 @@ def test_tuning_cache_file(tmp_path):
     assert len({k1, k2, k3}) == 3 and "512x512x512/r2c/f32/batch1/GPU A" == k1
     assert afft.tuning_cache_lookup(path, k1) is None
     afft.tuning_cache_store(path, k1, [4096, 1, 1, 0])
-    afft.tuning_cache_store(path, k2, [2048, 0, 1, 33554432])
-    assert afft.tuning_cache_lookup(path, k1) == [4096, 1, 1, 0]
-    assert afft.tuning_cache_lookup(path, k2) == [2048, 0, 1, 33554432]
+    afft.tuning_cache_store(path, k2, [2048, 0, 1, 33554432, 0, 1])
+    assert afft.tuning_cache_lookup(path, k1) == [4096, 1, 1, 0, 0, 0]      # a 4-entry record, padded
+    assert afft.tuning_cache_lookup(path, k2) == [2048, 0, 1, 33554432, 0, 1]
     assert afft.tuning_cache_lookup(path, k3) is None
-    afft.tuning_cache_store(path, k1, [1024, 0, 0, 0])
-    assert afft.tuning_cache_lookup(path, k1) == [1024, 0, 0, 0]
+    afft.tuning_cache_store(path, k1, [1024, 0, 0, 0, 0, 0])
+    assert afft.tuning_cache_lookup(path, k1) == [1024, 0, 0, 0, 0, 0]
     with open(path, "w") as fh:
         fh.write('{"%s": [1, 2]}' % k1)
     assert afft.tuning_cache_lookup(path, k1) is None
     with open(path, "w") as fh:
         fh.write("not json")
     assert afft.tuning_cache_lookup(path, k1) is None
-    afft.tuning_cache_store(path, k1, [4096, 1, 1, 0])
-    assert afft.tuning_cache_lookup(path, k1) == [4096, 1, 1, 0]
+    afft.tuning_cache_store(path, k1, [4096, 1, 1, 0, 1, 0])
+    assert afft.tuning_cache_lookup(path, k1) == [4096, 1, 1, 0, 1, 0]
 
 
 def test_noalloc_source_calls_no_allocator():

@@ -153,6 +153,26 @@ def test_r2c_odd_width_rows(shape):
            TOL["f32"])
 
 
+@pytest.mark.parametrize("shape", [(8, 512, 512), (4, 256, 64), (6, 48, 36), (5, 160, 72)])
+def test_r2c_odd_width_rows_early_release(shape):
+    """The row-pair N1 tiles with their load buffer released after the first pass (a tuning
+    choice): the same results as the oracle, both directions."""
+    x = synth.uniform_real(shape, 33).astype(np.float32)
+    ref = oracle.r2c(x)
+    H = ref.astype(np.complex64)
+    with afft.Plan(shape, "r2c", "f32") as p:
+        cfg = p.tuning
+        cfg[5] = 1
+        p.set_tuning(cfg)
+        assert p.describe()["rp_early"][1] == 1
+        X = p.forward(torch.from_numpy(x).cuda())
+        y = p.backward(torch.from_numpy(H).cuda())
+        torch.cuda.synchronize()
+    report("r2c odd rows early release %s" % (shape,), oracle.rel_l2(X.cpu().numpy(), ref), TOL["f32"])
+    report("c2r odd rows early release %s" % (shape,), oracle.rel_l2(y.cpu().numpy(), oracle.c2r(H, shape[2])),
+           TOL["f32"])
+
+
 @pytest.mark.parametrize("shape", [(3, 2, 8192), (8, 10, 160), (4, 6, 500)])
 def test_c2r_staged_and_direct_tiles(shape):
     """The specialised complex64 c2r kernels copy a CTA's run of half-spectrum lines into shared
