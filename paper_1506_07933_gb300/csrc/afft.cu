@@ -340,6 +340,18 @@ int upload_twiddles(afft_plan *p, const std::vector<int> &tm, const std::vector<
     return cuda_status(e);
 }
 
+// Lets `fn` use up to `bytes` of dynamic shared memory, capped at what the device's opt-in
+// maximum leaves beside the kernel's static shared memory (the tensor-core split kernels
+// hold a few KB of it).
+cudaError_t allow_dynamic_smem(const void *fn, int bytes, int max_smem)
+{
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, fn);
+    if (e != cudaSuccess) return e;
+    const int cap = max_smem - (int)attr.sharedSizeBytes;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, std::min(bytes, cap));
+}
+
 template <typename V>
 int plan_shapes(afft_plan *p)
 {
@@ -440,8 +452,7 @@ int plan_shapes(afft_plan *p)
                                fa.launch))
                 return AFFT_ERR_UNSUPPORTED;
             for (int k = 0; k < 2; ++k)
-                if (cudaFuncSetAttribute(fa.ks->four[k], cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) !=
-                    cudaSuccess)
+                if (allow_dynamic_smem(fa.ks->four[k], max_smem, max_smem) != cudaSuccess)
                     return AFFT_ERR_CUDA;
         }
     }
@@ -449,8 +460,7 @@ int plan_shapes(afft_plan *p)
     (void)y;
     for (int a = 0; a < 3; ++a)
         for (int k = 0; k < KS_COUNT; ++k) {
-            const cudaError_t e = cudaFuncSetAttribute(p->ax[a].ks->fn[k],
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+            const cudaError_t e = allow_dynamic_smem(p->ax[a].ks->fn[k], max_smem, max_smem);
             if (e != cudaSuccess) return AFFT_ERR_CUDA;
         }
     return AFFT_OK;

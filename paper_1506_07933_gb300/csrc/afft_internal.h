@@ -165,7 +165,9 @@ struct PlanView {
 };
 bool plan_view(const afft_plan *p, PlanView *v);
 const KernelSet *spec_kernels_split(int n);
-constexpr size_t kSplitTableBytes = 2 * 32 * 32 * sizeof(unsigned);
+// the mma.sync fragments (2 directions x 32 lanes x 32 words), then the tcgen05 operands
+// F_hi, F_lo of both directions in the canonical shared-memory layout (2 x 2 x 2 KB)
+constexpr size_t kSplitTableBytes = 2 * 32 * 32 * sizeof(unsigned) + 2 * 2 * 32 * 64;
 cudaError_t split_fragments(unsigned *table, cudaStream_t stream);
 
 }  // namespace afft

@@ -283,8 +283,8 @@ template <typename V, typename CT = V> struct TileOut {
 // and writes the other one; the last pass writes the stage's output.  Split:
 // radix-16 passes of complex64 tiles on the tensor cores (fft_split.cuh, table
 // `mma` of both directions).
-template <class Sh, int S, int N, int Ns, int TwOff, int Q, bool Split = false, bool TwSmem = false, typename V,
-          class Out, int R, int... Rest>
+template <class Sh, int S, int N, int Ns, int TwOff, int Q, bool Split = false, bool TwSmem = false, bool TC = false,
+          typename V, class Out, int R, int... Rest>
 __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V *tw, const Out &out,
                                             const unsigned *mma = nullptr)
 {
@@ -300,8 +300,8 @@ __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V
         const SmemRowsC<V, LG> in_rows{src};
         constexpr int B = Sh::per_thread(R);
         if constexpr (Last && Split && R == 16)
-            spec_pass<R, S, false, Split, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
-                                                 out.cols, mma);
+            spec_pass<R, S, false, Split, NT, B, TC>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                                     out.cols, mma, src);
         else if constexpr (Last && TwSmem)
             radix_pass<R, S, false, NT, B, true>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows, out.single);
         else if constexpr (TwSmem)
@@ -311,13 +311,13 @@ __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V
             spec_pass<R, S, false, Split, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
                                                  out.single, mma);
         else
-            spec_pass<R, S, false, Split, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
-                                                 SmemRowsC<V, LG>{dst}, mma);
+            spec_pass<R, S, false, Split, NT, B, TC>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                                     SmemRowsC<V, LG>{dst}, mma, src);
     }
     if constexpr (!Last) {
         __syncthreads();
         constexpr int next = TwOff + (Ns > 1 ? Ns * (R - 1) : 0);
-        pipe_passes<Sh, S, N, Ns * R, next, Q + 1, Split, TwSmem>(Seq<Rest...>{}, X, C, tw, out, mma);
+        pipe_passes<Sh, S, N, Ns * R, next, Q + 1, Split, TwSmem, TC>(Seq<Rest...>{}, X, C, tw, out, mma);
     }
 }
 
@@ -415,6 +415,11 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // split precision: radix-16 passes on tcgen05 where the tile allows (fft_tc.cuh)
+    constexpr bool TC = Split && sizeof(V) == 8;
+    if constexpr (TC)
+        tc_setup(reinterpret_cast<const unsigned char *>(mma) + kMmaTableWords * 4 + (S < 0 ? 0 : kTcBBytes),
+                 tc_cols_for(NT));
 
     auto issue = [&](long long tile, int b) {
         const long long o = tile / tiles_per_outer;
@@ -465,6 +470,7 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
                     // the other buffer's load, if one was issued, must land before the CTA exits
                     if (Early && tn < ntiles) mbar_wait_bounded(&bars[b ^ 1], (unsigned)(((i + 1) >> 1) & 1));
                 }
+                if constexpr (TC) tc_teardown();
                 return;
             }
         } else {
@@ -500,10 +506,14 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
                                                if (tn + gridDim.x < ntiles) issue(tn + gridDim.x, b);
                                            });
         } else if (!done) {
-            pipe_passes<Sh, S, N, 1, 0, 0, Split>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to, mma);
+            pipe_passes<Sh, S, N, 1, 0, 0, Split, false, TC>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to, mma);
         }
         if (tn >= ntiles) break;
         t = tn;
+    }
+    if constexpr (TC) {
+        if (tid == 0 && !tc_state().ok) atomicExch(err, 1u);   // a tensor-core wait ran out
+        tc_teardown();
     }
 }
 

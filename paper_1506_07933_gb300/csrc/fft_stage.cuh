@@ -31,6 +31,7 @@
 #include "afft_internal.h"
 #include "fft_access.cuh"
 #include "fft_split.cuh"
+#include "fft_tc.cuh"
 
 namespace afft {
 
@@ -113,46 +114,58 @@ template <int N, int... Rs> struct LinePlan {
 };
 
 // One pass of a specialised sequence: radix_pass, or with Split (complex64
-// split-precision families) the tensor-core radix-16 pass of fft_split.cuh.
-template <int R, int S, bool InPlace, bool Split, int NT = 0, int BM = 0, typename V, class Map, class Src,
-          class Dst>
+// split-precision families) a radix-16 pass on the tensor cores: tcgen05 (fft_tc.cuh) in
+// kernels that set up tensor memory (TC) when the tile allows it, staging in `stage`, else
+// mma.sync (fft_split.cuh).
+template <int R, int S, bool InPlace, bool Split, int NT = 0, int BM = 0, bool TC = false, typename V, class Map,
+          class Src, class Dst>
 __device__ __forceinline__ void spec_pass(int n, int Ns, const V *__restrict__ tw, int lines, const Map &map,
-                                          const Src &src, const Dst &dst, const unsigned *mma)
+                                          const Src &src, const Dst &dst, const unsigned *mma, void *stage = nullptr)
 {
-    if constexpr (Split && R == 16 && std::is_same<V, float2>::value)
+    if constexpr (Split && R == 16 && std::is_same<V, float2>::value) {
+        if constexpr (TC) {
+            if (tc_usable(lines * (n / 16))) {
+                tc16_pass<S>(n, Ns, tw, lines, map, src, dst, stage);
+                return;
+            }
+        }
         mma16_pass<S>(n, Ns, tw, lines, map, src, dst, mma + (S < 0 ? 0 : 32 * 32));
-    else
+    } else {
         radix_pass<R, S, InPlace, NT, BM>(n, Ns, tw, lines, map, src, dst);
+    }
 }
 
 // Runs passes Seq<R, Rest...> with Ns = product of the earlier radices and
 // TwOff = the table offset of this pass (the host lays tables out the same
 // way: Ns (R - 1) entries per pass with Ns > 1, in pass order).
-template <int S, bool First, bool LastToSmem, int N, int Ns, int TwOff, bool Split, typename V, class Map,
-          class Src, class Sm, class Dst, int R, int... Rest>
+template <int S, bool First, bool LastToSmem, int N, int Ns, int TwOff, bool Split, bool TC = false, typename V,
+          class Map, class Src, class Sm, class Dst, int R, int... Rest>
 __device__ __forceinline__ void run_passes(Seq<R, Rest...>, const V *tw, int lines, const Map &map,
                                            const Src &src, const Sm &sm, const Dst &dst, const unsigned *mma)
 {
     constexpr bool Last = sizeof...(Rest) == 0;
+    // tensor-core passes stage their operands in the CTA's shared tile (lines * n elements)
+    void *stage = nullptr;
+    if constexpr (TC) stage = sm.sm;
     if (!First) __syncthreads();
     if constexpr (First && Last) {
-        if constexpr (LastToSmem) spec_pass<R, S, false, Split>(N, Ns, tw + TwOff, lines, map, src, sm, mma);
-        else spec_pass<R, S, false, Split>(N, Ns, tw + TwOff, lines, map, src, dst, mma);
+        if constexpr (LastToSmem) spec_pass<R, S, false, Split, 0, 0, TC>(N, Ns, tw + TwOff, lines, map, src, sm, mma, stage);
+        else spec_pass<R, S, false, Split, 0, 0, TC>(N, Ns, tw + TwOff, lines, map, src, dst, mma, stage);
     } else if constexpr (First) {
-        spec_pass<R, S, false, Split>(N, Ns, tw + TwOff, lines, map, src, sm, mma);
+        spec_pass<R, S, false, Split, 0, 0, TC>(N, Ns, tw + TwOff, lines, map, src, sm, mma, stage);
     } else if constexpr (Last && !LastToSmem) {
-        spec_pass<R, S, false, Split>(N, Ns, tw + TwOff, lines, map, sm, dst, mma);
+        spec_pass<R, S, false, Split, 0, 0, TC>(N, Ns, tw + TwOff, lines, map, sm, dst, mma, stage);
     } else {
-        spec_pass<R, S, true, Split>(N, Ns, tw + TwOff, lines, map, sm, sm, mma);
+        spec_pass<R, S, true, Split, 0, 0, TC>(N, Ns, tw + TwOff, lines, map, sm, sm, mma, stage);
     }
     if constexpr (!Last) {
         constexpr int next = TwOff + (Ns > 1 ? Ns * (R - 1) : 0);
-        run_passes<S, false, LastToSmem, N, Ns * R, next, Split>(Seq<Rest...>{}, tw, lines, map, src, sm, dst, mma);
+        run_passes<S, false, LastToSmem, N, Ns * R, next, Split, TC>(Seq<Rest...>{}, tw, lines, map, src, sm, dst, mma);
     }
 }
 
-template <class P, int S, bool LastToSmem, bool Split = false, typename V, class Map, class Src, class Sm,
-          class Dst>
+template <class P, int S, bool LastToSmem, bool Split = false, bool TC = false, typename V, class Map, class Src,
+          class Sm, class Dst>
 __device__ __forceinline__ void run_plan(const V *tw, int lines, const Map &map, const Src &src,
                                          const Sm &sm, const Dst &dst, const unsigned *mma = nullptr)
 {
@@ -162,7 +175,7 @@ __device__ __forceinline__ void run_plan(const V *tw, int lines, const Map &map,
             else dst(idx, 0, src(idx, 0));
         }
     } else {
-        run_passes<S, true, LastToSmem, P::n, 1, 0, Split>(typename P::seq{}, tw, lines, map, src, sm, dst, mma);
+        run_passes<S, true, LastToSmem, P::n, 1, 0, Split, TC>(typename P::seq{}, tw, lines, map, src, sm, dst, mma);
     }
 }
 
@@ -377,7 +390,15 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
             }
         }
         const SmemLines<V> tile{sm, n};
-        run_plan<typename F::plan, S, false, F::split>(tw, lines, map, src, tile, dst, d.mma);
+        if constexpr (F::split && std::is_same<V, float2>::value) {
+            // split precision: radix-16 passes on tcgen05 (fft_tc.cuh) where the CTA allows
+            tc_setup(reinterpret_cast<const unsigned char *>(d.mma) + kMmaTableWords * 4 + (S < 0 ? 0 : kTcBBytes),
+                     tc_cols_for((int)blockDim.x));
+            run_plan<typename F::plan, S, false, true, true>(tw, lines, map, src, tile, dst, d.mma);
+            tc_teardown();
+        } else {
+            run_plan<typename F::plan, S, false, F::split>(tw, lines, map, src, tile, dst, d.mma);
+        }
     }
 }
 
