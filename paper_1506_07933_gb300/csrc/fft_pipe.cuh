@@ -179,6 +179,13 @@ template <class P, typename V> struct PipeShape {
     static constexpr int smem_rp = (2 * tile_rp + tile) * (int)sizeof(V) + 16 + tw_smem * 8;
     static constexpr bool rp_ok = sizeof(V) == 8 && lines == 16 && P::n % 16 == 0 && P::n / 2 <= 256;
     static constexpr int box_rows = tma_box_rows(P::n);
+    // split precision: the radix-16 passes' butterflies (tile / 16) fill whole 128-row blocks and
+    // one 128-thread group per block covers them -- the tcgen05 pass runs unconditionally
+    static constexpr bool tc_tile = sizeof(V) == 8 && (tile / 16) % 128 == 0 && threads % 128 == 0 &&
+                                    tile / 16 <= threads && threads <= 512;
+    // CTAs per SM the launch bounds ask for: two when two such CTAs' shared memory fits (tiles,
+    // table and the tensor-core state, about 5 KB of static shared memory)
+    static constexpr int min_blocks_split = 2 * (smem + 6 * 1024) <= 226 * 1024 ? 2 : 1;
     static_assert((box_rows * lines * (int)sizeof(V)) % 128 == 0 || box_rows == P::n,
                   "TMA boxes must start 128-byte aligned in shared memory");
 };
@@ -283,7 +290,7 @@ template <typename V, typename CT = V> struct TileOut {
 // and writes the other one; the last pass writes the stage's output.  Split:
 // radix-16 passes of complex64 tiles on the tensor cores (fft_split.cuh, table
 // `mma` of both directions).
-template <class Sh, int S, int N, int Ns, int TwOff, int Q, bool Split = false, bool TwSmem = false, bool TC = false,
+template <class Sh, int S, int N, int Ns, int TwOff, int Q, bool Split = false, bool TwSmem = false, int TC = 0,
           typename V, class Out, int R, int... Rest>
 __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V *tw, const Out &out,
                                             const unsigned *mma = nullptr)
@@ -300,8 +307,11 @@ __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V
         const SmemRowsC<V, LG> in_rows{src};
         constexpr int B = Sh::per_thread(R);
         if constexpr (Last && Split && R == 16)
-            spec_pass<R, S, false, Split, NT, B, TC>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
-                                                     out.cols, mma, src);
+            spec_pass<R, S, false, Split, NT, B, TC, TwSmem>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                                             out.cols, mma, src);
+        else if constexpr (Split && R == 16)
+            spec_pass<R, S, false, Split, NT, B, TC, TwSmem>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                                             SmemRowsC<V, LG>{dst}, mma, src);
         else if constexpr (Last && TwSmem)
             radix_pass<R, S, false, NT, B, true>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows, out.single);
         else if constexpr (TwSmem)
@@ -311,8 +321,8 @@ __device__ __forceinline__ void pipe_passes(Seq<R, Rest...>, V *X, V *C, const V
             spec_pass<R, S, false, Split, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
                                                  out.single, mma);
         else
-            spec_pass<R, S, false, Split, NT, B, TC>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
-                                                     SmemRowsC<V, LG>{dst}, mma, src);
+            spec_pass<R, S, false, Split, NT, B>(N, Ns, tw + TwOff, Sh::lines, MapLineFastC<LG>{}, in_rows,
+                                                 SmemRowsC<V, LG>{dst}, mma);
     }
     if constexpr (!Last) {
         __syncthreads();
@@ -383,7 +393,7 @@ __device__ __forceinline__ bool pipe_df(Seq<R0, Rest...>, double2 *X, double2 *C
 // ---------------------------------------------------------------- kernel ---
 
 template <class P, int S, typename V, bool TMA, bool Split = false, bool Blocked = false>
-__global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
+__global__ void __launch_bounds__(PipeShape<P, V>::threads, Split ? PipeShape<P, V>::min_blocks_split : 1)
     k_strided_pipe(const V *__restrict__ in, V *out, const __grid_constant__ CUtensorMap tmap,
                    const V *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
                    unsigned *err, const void *twdf, const unsigned *mma, int zrows, long long zstride)
@@ -406,7 +416,8 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     // those tiles read their twiddles from a copy of the line's table in shared memory, staged
     // once per CTA (the factors of a pass are the same for every tile)
     float2 *const tw_s = reinterpret_cast<float2 *>(pipe_smem_raw + 3 * TILE_BYTES + 16);
-    if constexpr (Early) {
+    constexpr bool StageTw = Early || (Split && sizeof(V) == 8);
+    if constexpr (StageTw) {
         for (int e = tid; e < Sh::tw_smem; e += NT) tw_s[e] = ldgc(reinterpret_cast<const float2 *>(tw) + e);
     }
     if (TMA && tid == 0) {
@@ -506,7 +517,11 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
                                                if (tn + gridDim.x < ntiles) issue(tn + gridDim.x, b);
                                            });
         } else if (!done) {
-            pipe_passes<Sh, S, N, 1, 0, 0, Split, false, TC>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to, mma);
+            if constexpr (TC)
+                pipe_passes<Sh, S, N, 1, 0, 0, Split, true, Sh::tc_tile ? 2 : 1>(
+                    typename P::seq{}, buf0 + b * TILE, scratch, reinterpret_cast<const V *>(tw_s), to, mma);
+            else
+                pipe_passes<Sh, S, N, 1, 0, 0, Split>(typename P::seq{}, buf0 + b * TILE, scratch, tw, to, mma);
         }
         if (tn >= ntiles) break;
         t = tn;

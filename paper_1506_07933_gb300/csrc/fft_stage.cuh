@@ -115,30 +115,35 @@ template <int N, int... Rs> struct LinePlan {
 
 // One pass of a specialised sequence: radix_pass, or with Split (complex64
 // split-precision families) a radix-16 pass on the tensor cores: tcgen05 (fft_tc.cuh) in
-// kernels that set up tensor memory (TC) when the tile allows it, staging in `stage`, else
-// mma.sync (fft_split.cuh).
-template <int R, int S, bool InPlace, bool Split, int NT = 0, int BM = 0, bool TC = false, typename V, class Map,
-          class Src, class Dst>
+// kernels that set up tensor memory, staging in `stage` -- TC = 1: when the tile allows it
+// (checked at run time), else mma.sync (fft_split.cuh); TC = 2: always (the kernel's tile
+// shape qualifies at compile time).  TwSmem: twiddles from a shared-memory table.
+template <int R, int S, bool InPlace, bool Split, int NT = 0, int BM = 0, int TC = 0, bool TwSmem = false,
+          typename V, class Map, class Src, class Dst>
 __device__ __forceinline__ void spec_pass(int n, int Ns, const V *__restrict__ tw, int lines, const Map &map,
                                           const Src &src, const Dst &dst, const unsigned *mma, void *stage = nullptr)
 {
     if constexpr (Split && R == 16 && std::is_same<V, float2>::value) {
-        if constexpr (TC) {
-            if (tc_usable(lines * (n / 16))) {
-                tc16_pass<S>(n, Ns, tw, lines, map, src, dst, stage);
-                return;
+        if constexpr (TC == 2) {
+            tc16_pass<S, TwSmem>(n, Ns, tw, lines, map, src, dst, stage);
+        } else {
+            if constexpr (TC == 1) {
+                if (tc_usable(lines * (n / 16))) {
+                    tc16_pass<S, TwSmem>(n, Ns, tw, lines, map, src, dst, stage);
+                    return;
+                }
             }
+            mma16_pass<S>(n, Ns, tw, lines, map, src, dst, mma + (S < 0 ? 0 : 32 * 32));
         }
-        mma16_pass<S>(n, Ns, tw, lines, map, src, dst, mma + (S < 0 ? 0 : 32 * 32));
     } else {
-        radix_pass<R, S, InPlace, NT, BM>(n, Ns, tw, lines, map, src, dst);
+        radix_pass<R, S, InPlace, NT, BM, TwSmem>(n, Ns, tw, lines, map, src, dst);
     }
 }
 
 // Runs passes Seq<R, Rest...> with Ns = product of the earlier radices and
 // TwOff = the table offset of this pass (the host lays tables out the same
 // way: Ns (R - 1) entries per pass with Ns > 1, in pass order).
-template <int S, bool First, bool LastToSmem, int N, int Ns, int TwOff, bool Split, bool TC = false, typename V,
+template <int S, bool First, bool LastToSmem, int N, int Ns, int TwOff, bool Split, int TC = 0, typename V,
           class Map, class Src, class Sm, class Dst, int R, int... Rest>
 __device__ __forceinline__ void run_passes(Seq<R, Rest...>, const V *tw, int lines, const Map &map,
                                            const Src &src, const Sm &sm, const Dst &dst, const unsigned *mma)
@@ -164,7 +169,7 @@ __device__ __forceinline__ void run_passes(Seq<R, Rest...>, const V *tw, int lin
     }
 }
 
-template <class P, int S, bool LastToSmem, bool Split = false, bool TC = false, typename V, class Map, class Src,
+template <class P, int S, bool LastToSmem, bool Split = false, int TC = 0, typename V, class Map, class Src,
           class Sm, class Dst>
 __device__ __forceinline__ void run_plan(const V *tw, int lines, const Map &map, const Src &src,
                                          const Sm &sm, const Dst &dst, const unsigned *mma = nullptr)
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
             // split precision: radix-16 passes on tcgen05 (fft_tc.cuh) where the CTA allows
             tc_setup(reinterpret_cast<const unsigned char *>(d.mma) + kMmaTableWords * 4 + (S < 0 ? 0 : kTcBBytes),
                      tc_cols_for((int)blockDim.x));
-            run_plan<typename F::plan, S, false, true, true>(tw, lines, map, src, tile, dst, d.mma);
+            run_plan<typename F::plan, S, false, true, 1>(tw, lines, map, src, tile, dst, d.mma);
             tc_teardown();
         } else {
             run_plan<typename F::plan, S, false, F::split>(tw, lines, map, src, tile, dst, d.mma);

@@ -198,7 +198,7 @@ __device__ __forceinline__ bool tc_usable(int total)
 // writes (j - j mod Ns) 16 + j mod Ns + s Ns) with the products on the tensor cores.  stage:
 // shared memory of at least total * 128 bytes that may be overwritten once every thread has
 // read its inputs (the source tile itself is fine).
-template <int S, class Map, class Src, class Dst>
+template <int S, bool TwSmem = false, class Map, class Src, class Dst>
 __device__ __forceinline__ void tc16_pass(int n, int Ns, const float2 *__restrict__ tw, int lines, const Map &map,
                                           const Src &src, const Dst &dst, void *stage)
 {
@@ -217,7 +217,7 @@ __device__ __forceinline__ void tc16_pass(int n, int Ns, const float2 *__restric
         if (Ns > 1) {
             const float2 *w = tw + (j % Ns) * 15;
 #pragma unroll
-            for (int r = 1; r < 16; ++r) x[r] = ctw<S>(x[r], ldgc(w + r - 1));
+            for (int r = 1; r < 16; ++r) x[r] = ctw<S>(x[r], tw_ld<TwSmem>(w + r - 1));
         }
         float m = 0.f;
 #pragma unroll
