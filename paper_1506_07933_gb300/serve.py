@@ -15,9 +15,15 @@ scheduling step:
   slot's stream.  A batch gathers its members' right-hand sides into the
   plan's contiguous input (a device copy); a single request is solved in
   place from its own buffer;
-* groups of different sizes run on different streams and overlap on the GPU;
-  small groups go to high-priority streams (their thread blocks are
-  dispatched ahead of a large solve's), large ones to normal-priority ones.
+* groups of different sizes run on different streams and overlap on the GPU.
+  Large groups (at least `large_bytes` of field) run one at a time, in
+  arrival order, on one normal-priority lane, so that they neither wait for
+  small requests nor share the GPU with another large solve; small groups run
+  on the other lanes, high-priority streams whose thread blocks are
+  dispatched ahead of the large solve's (and on the large lane while no large
+  request waits).  A small queue whose head has waited longer than `age_ms`
+  is admitted first.  While nothing runs, the loop spins up to the next
+  arrival instead of sleeping through it.
 
 `run_plain` serves the same requests one at a time on one stream with a
 (cached) single plan per size: the plain one-plan-per-request form the
@@ -162,13 +168,18 @@ class PoissonServer:
 
     def __init__(self, pool: RhsPool, slots: int = 4, hbm_budget: int = None, max_batch_bytes: int = 64 << 20,
                  max_batch: int = 16, policy: str = "sjf", large_bytes: int = 256 << 20,
-                 age_ms: float = 8.0):
+                 age_ms: float = 8.0, large_first: bool = False, small_beside_large: int = None):
         self.pool = pool
-        # slots [0, slots/2) are high-priority streams for small groups; the rest take large ones
+        # small groups in flight while a large solve runs (None: every small lane)
+        self.small_beside_large = small_beside_large
+        # slots [0, slots - 1) take small groups, the last one is the lane of large groups (with one
+        # slot, it takes everything); the small lanes' streams have the higher priority, or the
+        # large lane's with large_first
         lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
-        self.n_fast = slots // 2
-        self.slots = [torch.cuda.Stream(priority=hi) for _ in range(self.n_fast)] + \
-                     [torch.cuda.Stream(priority=lo) for _ in range(slots - self.n_fast)]
+        small_p, large_p = (lo, hi) if large_first else (hi, lo)
+        self.n_fast = max(0, slots - 1)
+        self.slots = [torch.cuda.Stream(priority=small_p) for _ in range(self.n_fast)] + \
+                     [torch.cuda.Stream(priority=large_p) for _ in range(slots - self.n_fast)]
         self.policy = policy
         self.large_bytes = large_bytes
         self.age = age_ms * 1e-3   # a head request older than this is admitted first ("sjf")
@@ -181,10 +192,13 @@ class PoissonServer:
         self.results = {}
         self.alloc_failures = 0   # plan or buffer allocations the device refused
 
+    def _large(self, n, prec, B=1):
+        return B * n ** 3 * BYTES[prec] >= self.large_bytes
+
     def _order(self, queue, now=None):
         """Waiting (n, precision) queues in admission order: oldest head first ("fifo"), or
         smallest group work first, ties by age ("sjf"), except that queues whose head has waited
-        longer than `age_ms` go first, oldest first (so large solves are not starved)."""
+        longer than `age_ms` go first, oldest first."""
         keys = [k for k, q in queue.items() if q]
         if self.policy == "fifo":
             return sorted(keys, key=lambda k: queue[k][0].arrival)
@@ -263,14 +277,13 @@ class PoissonServer:
 
     def _launch(self, group, entry, stream):
         plan, f, u = entry
+        if len(group) == 1:   # solved from its own right-hand side
+            plan.poisson(self.pool.rhs(group[0]), u, stream=stream)
+            return
         with torch.cuda.stream(stream):
-            if len(group) == 1:
-                src = self.pool.rhs(group[0])
-            else:
-                for b, r in enumerate(group):
-                    f[b].copy_(self.pool.rhs(r), non_blocking=True)
-                src = f
-            plan.poisson(src, u, stream=stream)
+            for b, r in enumerate(group):
+                f[b].copy_(self.pool.rhs(r), non_blocking=True)
+            plan.poisson(f, u, stream=stream)
 
     def warm(self, sizes, precisions=("f32", "f64")):
         """Create (and run once on every slot stream) the plans the batch sizes of these sizes need,
@@ -309,14 +322,17 @@ class PoissonServer:
         done = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        changed = True
         while pending or any(queue.values()) or busy:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 r = pending.popleft()
                 queue[(r.n, r.precision)].append(r)
+                changed = True
             for si in list(busy):
                 ev, group, entry, key = busy[si]
                 if ev.query():
+                    changed = True
                     t = time.perf_counter() - t0
                     u = entry[2]
                     for b, r in enumerate(group):
@@ -326,25 +342,20 @@ class PoissonServer:
                     self._give(key, entry)
                     done.append((group, key))
                     del busy[si]
+            if not changed:
+                continue    # nothing arrived and nothing finished: poll again
+            changed = False
             free_slots = [i for i in range(len(self.slots)) if i not in busy]
             now = time.perf_counter() - t0
-            for (n, prec) in self._order(queue, now):
-                if not free_slots:
-                    break
-                q = queue[(n, prec)]
+
+            def admit(key, si):
+                n, prec = key
+                q = queue[key]
                 B = self._batch(n, prec, len(q))
-                large = B * n ** 3 * BYTES[prec] >= self.large_bytes
-                overdue = now - q[0].arrival > self.age
-                # large groups run on the normal-priority slots; small ones, and any group whose
-                # head is overdue, prefer the high-priority slots, whose kernels are dispatched first
-                usable = [i for i in free_slots if i >= self.n_fast] if (large and not overdue) else free_slots
-                if not usable:
-                    continue
                 entry = self._take(n, prec, B)
                 if entry is None:
-                    continue
+                    return False
                 group = [q.popleft() for _ in range(B)]
-                si = usable[0]
                 free_slots.remove(si)
                 t = time.perf_counter() - t0
                 for r in group:
@@ -353,11 +364,34 @@ class PoissonServer:
                 ev = torch.cuda.Event()
                 ev.record(self.slots[si])
                 busy[si] = (ev, group, entry, (n, prec, B))
+                return True
+
+            lane = len(self.slots) - 1          # the large groups' lane
+            large_keys = [k for k, q in queue.items() if q and self._large(*k)]
+            if lane in free_slots and large_keys:
+                # the oldest waiting large request, alone on its lane
+                admit(min(large_keys, key=lambda k: queue[k][0].arrival), lane)
+            for key in self._order(queue, now):
+                if not free_slots:
+                    break
+                if self._large(*key):
+                    continue
+                if (self.small_beside_large is not None and lane in busy and busy[lane][3][0:2] and
+                        self._large(*busy[lane][3][0:2]) and
+                        sum(1 for i in busy if i != lane) >= self.small_beside_large):
+                    break   # enough small work beside the running large solve
+                # small groups: the high-priority slots, or the large lane while no large request waits
+                usable = [i for i in free_slots if i != lane or not (large_keys or lane in busy)]
+                if usable:
+                    admit(key, usable[0])
             if not busy and any(queue.values()):
                 # nothing runs and nothing could be admitted: no memory will free up
                 raise MemoryError("cannot admit any waiting request: the device refused every allocation")
             if not busy and not any(queue.values()) and pending:
-                time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.0005)))
+                # idle: sleep until about a millisecond before the next arrival, then spin
+                gap = pending[0].arrival - (time.perf_counter() - t0)
+                if gap > 0.002:
+                    time.sleep(gap - 0.001)
         wall = time.perf_counter() - t0
         served = [r for g, _ in done for r in g]
         if check_results:
