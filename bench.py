@@ -798,6 +798,46 @@ def cufft_reference(torch, peak):
     return out
 
 
+def run_case(args):
+    """One configuration, `kind:n0xn1xn2:precision` (e.g. c2c:256x256x256:f64): W warm-up and K
+    timed forward + backward transforms of a seeded uniform input on one GPU, one JSON line with
+    the per-stage times.  For profiling single stage kernels; not the benchmark's metric line."""
+    import torch
+    from paper_1506_07933_gb300 import afft
+    from paper_1506_07933_gb300 import build as libbuild
+    kind, dims, prec = args.case.split(":")
+    shape = tuple(int(v) for v in dims.split("x"))
+    torch.cuda.set_device(0)
+    libbuild.build()
+    afft.load()
+    p = afft.Plan(shape, kind, prec)
+    x = torch.empty(p.spatial_shape, dtype=p.spatial_dtype, device="cuda")
+    if kind == "c2c":
+        afft.fill_uniform(x, 10240)
+    else:
+        x.uniform_(-1, 1)
+    X = torch.empty(p.spectral_shape, dtype=p.spectral_dtype, device="cuda")
+    y = torch.empty(p.spatial_shape, dtype=p.spatial_dtype, device="cuda")
+    for _ in range(args.warmup):
+        p.forward(x, X)
+        p.backward(X, y)
+    torch.cuda.synchronize()
+    p.timing_begin(2 * args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        p.forward(x, X)
+        p.backward(X, y)
+    e1.record()
+    torch.cuda.synchronize()
+    st = p.timing_end()
+    fwd = [sum(r[i] for r in st[0::2]) / args.steps for i in range(3)]
+    bwd = [sum(r[i] for r in st[1::2]) / args.steps for i in range(3)]
+    print(json.dumps({"case": args.case, "ms_per_step": e0.elapsed_time(e1) / args.steps, "stage_ms_forward": fwd,
+                      "stage_ms_backward": bwd, "plan": p.describe()}), flush=True)
+    p.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -809,6 +849,8 @@ def main():
                     help="leave out the metric's other configurations (the 'also' block)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--case", default=None,
+                    help="time one configuration kind:n0xn1xn2:precision instead (for profiling)")
     ap.add_argument("--decomp", choices=["plan", "slab", "replicas"], default=None,
                     help="one plan per GPU at N = 1 (default), slab decomposition (default at N > 1) "
                          "or independent replicas per GPU")
@@ -817,6 +859,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.case:
+        run_case(args)
     else:
         run_gpu(args)
 

@@ -1687,7 +1687,7 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         "\"radix\": [\"%s\", \"%s\", \"%s\"], \"specialised\": [%d, %d, %d], \"four_step\": [%d, %d, %d], "
         "\"pipelined\": [%d, %d], \"contig_lines\": %d, \"strided_lines\": [%d, %d], "
         "\"l2_slab_planes\": %d, \"blocked\": %d, \"axes\": %d, \"backward_scale\": %.17g, "
-        "\"rp_early\": [%d, %d], "
+        "\"rp_early\": [%d, %d], \"pipe_ctas\": [%d, %d], "
         "\"stage_kernels_forward\": [\"%s\", \"%s\", \"%s\"], \"stage_kernels_backward\": [\"%s\", \"%s\", \"%s\"]}",
         (long long)p->n[0], (long long)p->n[1], (long long)p->n[2], (long long)p->batch,
         p->kind == AFFT_C2C ? "c2c" : "r2c",
@@ -1696,7 +1696,7 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         p->four[2].on, p->ax[0].pipe, p->ax[1].pipe, p->ax[2].launch.lines,
         p->ax[0].pipe ? p->ax[0].ks->pipe_lines : p->ax[0].launch.lines,
         p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, p->chunk_planes, (int)blk, p->axes, p->bscale,
-        (int)p->ax[0].rp_early, (int)p->ax[1].rp_early,
+        (int)p->ax[0].rp_early, (int)p->ax[1].rp_early, p->ax[0].pipe_slots, p->ax[1].pipe_slots,
         blk ? "k_contig" : zf, y, x, x, y, blk ? "k_contig" : zb);
     if (need < 0) return AFFT_ERR_CUDA;
     return (size_t)need < len ? AFFT_OK : AFFT_ERR_SIZE;
