@@ -352,6 +352,30 @@ cudaError_t allow_dynamic_smem(const void *fn, int bytes, int max_smem)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, std::min(bytes, cap));
 }
 
+// CTAs of `fn` resident on one SM, from its registers, shared memory and threads alone.  The
+// runtime's occupancy query returns 1 for the kernels that allocate tensor memory, whatever
+// their resources (measured on 256-point split stages: 79 registers, 105 KB of shared memory,
+// two CTAs resident and 22% faster than one when the grid holds two per SM).  Tensor memory
+// itself does not limit them: a CTA allocates 64 to 128 of the SM's 512 columns.
+int resident_per_sm(const void *fn, int threads, int dyn_smem, int device)
+{
+    cudaFuncAttributes fa;
+    int smem_sm = 0, reserved = 0, thr_sm = 0, blk_sm = 0, regs_sm = 0;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, device) != cudaSuccess)
+        return 0;
+    const int warps = (threads + 31) / 32;
+    // registers go to warps in units of 256, and each of the four schedulers holds a quarter
+    const int warp_regs = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;
+    const int by_regs = (regs_sm / 4 / warp_regs) * 4 / warps;
+    const int by_smem = smem_sm / ((int)fa.sharedSizeBytes + dyn_smem + reserved);
+    return std::min(std::min(by_regs, by_smem), std::min(thr_sm / (warps * 32), blk_sm));
+}
+
 template <typename V>
 int plan_shapes(afft_plan *p)
 {
@@ -391,8 +415,14 @@ int plan_shapes(afft_plan *p)
                 return AFFT_ERR_CUDA;
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks->pipe[PIPE_FWD_TMA], ks->pipe_threads,
-                                                          ks->pipe_smem) != cudaSuccess || per_sm < 1)
+                                                          ks->pipe_smem) != cudaSuccess)
             continue;
+        // the split kernels hold tensor memory; their CTAs never wait on one another, so a grid
+        // above what is resident is still correct
+        if (p->precision == AFFT_F32_SPLIT)
+            per_sm = std::max(per_sm, resident_per_sm(ks->pipe[PIPE_FWD_TMA], ks->pipe_threads, ks->pipe_smem,
+                                                      p->device));
+        if (per_sm < 1) continue;
         ap.pipe_slots = sms * per_sm;   // also what the blocked c2c layout runs with
         // rows far apart: the many CTAs of the plain kernel win in the row-major layout
         const bool far = ks->n >= 1024 && row_bytes[a] > (1LL << 22);

@@ -140,11 +140,13 @@ def test_ragged_tiles(shape, prec):
 
 @pytest.mark.parametrize("shape", [(16, 24, 40), (64, 48, 96), (32, 3, 96), (120, 8, 12), (8, 1, 24),
                                    (8, 512, 512), (4, 256, 64), (6, 48, 36), (2, 32, 8), (3, 16, 120),
-                                   (5, 160, 72), (2, 384, 40)])
+                                   (5, 160, 72), (2, 384, 40), (5, 32, 108), (40, 64, 64)])
 def test_r2c_odd_width_rows(shape):
     """FP32 r2c plans whose half-spectrum width n2/2+1 is odd: complex64 rows of odd width,
     read as row pairs through TMA in the N1 stage where n1 allows (a multiple of 16, at most
-    512), by per-element copies otherwise; results must not change."""
+    512), by per-element copies otherwise; results must not change.  The last tile of each row
+    holds W mod 16 columns: one (W = 49, 257, 33), three (19), five (37, 21), seven (55) or
+    thirteen (61)."""
     x = synth.uniform_real(shape, 31).astype(np.float32)
     ref = oracle.r2c(x)
     report("r2c odd rows %s f32" % (shape,), oracle.rel_l2(gpu_r2c(x, "f32"), ref), TOL["f32"])
@@ -153,7 +155,8 @@ def test_r2c_odd_width_rows(shape):
            TOL["f32"])
 
 
-@pytest.mark.parametrize("shape", [(8, 512, 512), (4, 256, 64), (6, 48, 36), (5, 160, 72)])
+@pytest.mark.parametrize("shape", [(8, 512, 512), (4, 256, 64), (6, 48, 36), (5, 160, 72), (5, 32, 108),
+                                   (40, 64, 64)])
 def test_r2c_odd_width_rows_early_release(shape):
     """The row-pair N1 tiles with their load buffer released after the first pass (a tuning
     choice): the same results as the oracle, both directions."""
