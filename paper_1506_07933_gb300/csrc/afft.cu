@@ -1327,6 +1327,11 @@ int afft_plan_create_axes(afft_plan **out, const int64_t n[3], int64_t batch, in
             st = AFFT_ERR_NOMEM;
         } else if (cudaMemset(p->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
             st = AFFT_ERR_CUDA;
+        } else {
+            for (int a = 0; a < 3; ++a) {
+                p->ax[a].desc.err = p->d_err;
+                p->four[a].a.desc.err = p->d_err;
+            }
         }
     }
     if (st == AFFT_OK && precision == AFFT_F64 && p->d_tw) {

@@ -41,6 +41,7 @@ struct StageDesc {
     // ((j / blk) * planes + plane) * blk + j % blk; blk = 0: row-major on both sides
     int blk, blk_in, blk_out;
     long long blk_n1, blk_planes;
+    unsigned *err;                 // set by a kernel whose bounded wait ran out (null: not reported)
 };
 
 // Line of the blocked layout holding row-major line q (see StageDesc::blk).

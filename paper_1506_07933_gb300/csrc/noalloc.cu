@@ -24,6 +24,7 @@
 // names a host-side stand-in), so the first call on each device looks up the
 // device address with cudaGetSymbolAddress, with that device current, and
 // caches it.  That first call is the set-up: make it before any stream capture.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -249,20 +250,24 @@ int run(const int64_t n[3], int precision, const void *in, void *out, cudaStream
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (max_smem <= 0) max_smem = 48 * 1024;
-    auto budget = [&](const Axis &a) -> size_t {
-        return a.ks->generic ? (size_t)max_smem : (size_t)(max_smem < 112 * 1024 ? max_smem : 112 * 1024);
+    // the dynamic shared memory a kernel may take: the opt-in maximum less its static shared
+    // memory (the c2r kernels hold an mbarrier there)
+    const void *fns[3] = {ax[0].ks->fn[KS_STRIDED_BWD], ax[1].ks->fn[KS_STRIDED_BWD], ax[2].ks->fn[KS_C2R]};
+    int dyn_max[3];
+    for (int a = 0; a < 3; ++a) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, fns[a]) != cudaSuccess) return AFFT_ERR_CUDA;
+        dyn_max[a] = max_smem - (int)fa.sharedSizeBytes;
+    }
+    auto budget = [&](int a) -> size_t {
+        return ax[a].ks->generic ? (size_t)dyn_max[a] : (size_t)std::min(dyn_max[a], 112 * 1024);
     };
-    if (!shape_strided(ax[0], 1, n1 * nh, elem, budget(ax[0])) ||
-        !shape_strided(ax[1], n0, nh, elem, budget(ax[1])) ||
-        !shape_contig(ax[2], n0 * n1, elem, budget(ax[2]), elem == 8 && (nh & 1)))
+    if (!shape_strided(ax[0], 1, n1 * nh, elem, budget(0)) || !shape_strided(ax[1], n0, nh, elem, budget(1)) ||
+        !shape_contig(ax[2], n0 * n1, elem, budget(2), elem == 8 && (nh & 1)))
         return AFFT_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(ax[0].ks->fn[KS_STRIDED_BWD], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             max_smem) != cudaSuccess ||
-        cudaFuncSetAttribute(ax[1].ks->fn[KS_STRIDED_BWD], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             max_smem) != cudaSuccess ||
-        cudaFuncSetAttribute(ax[2].ks->fn[KS_C2R], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             max_smem) != cudaSuccess)
-        return AFFT_ERR_CUDA;
+    for (int a = 0; a < 3; ++a)
+        if (cudaFuncSetAttribute(fns[a], cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max[a]) != cudaSuccess)
+            return AFFT_ERR_CUDA;
 
     V *tw = (V *)scratch;
     V *work = (V *)(scratch + kTwiddleBytes);
