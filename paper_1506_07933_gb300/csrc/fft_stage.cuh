@@ -422,12 +422,15 @@ __device__ __forceinline__ void run_plan_staged(Seq<R0, Rest...>, const V *tw, i
     }
 }
 
-// Copies `elems` complex64 values from global memory (16-byte aligned) into
-// shared memory with one bulk copy (an 8-byte load for an odd tail) and waits
-// for them (all threads of the CTA; a one-shot mbarrier, the wait bounded).
-// Returns false, on every thread, if the copy did not land in time.
-__device__ __forceinline__ bool stage_contiguous(float2 *sm, const float2 *src, int elems)
+// Copies `elems` complex values (complex64 or complex128) from global memory
+// (16-byte aligned) into shared memory with one bulk copy (an 8-byte load for
+// an odd complex64 tail) and waits for them (all threads of the CTA; a
+// one-shot mbarrier, the wait bounded).  Returns false, on every thread, if
+// the copy did not land in time.
+template <typename V>
+__device__ __forceinline__ bool stage_contiguous(V *sm, const V *src, int elems)
 {
+    static_assert(sizeof(V) == 8 || sizeof(V) == 16, "complex64 or complex128");
     __shared__ __align__(8) unsigned long long bar;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -435,10 +438,10 @@ __device__ __forceinline__ bool stage_contiguous(float2 *sm, const float2 *src, 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned bytes = (unsigned)(elems / 2) * 16u;
+        const unsigned bytes = (unsigned)((size_t)elems * sizeof(V) / 16) * 16u;
         mbar_expect_tx(&bar, bytes);
         bulk_load_1d(sm, src, bytes, &bar);
-        if (elems & 1) sm[elems - 1] = __ldcg(src + elems - 1);
+        if (sizeof(V) == 8 && (elems & 1)) sm[elems - 1] = __ldcg(src + elems - 1);
     }
     const bool ok = mbar_wait_bounded(&bar, 0);
     return __syncthreads_or(!ok) == 0;
@@ -613,13 +616,21 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
         if constexpr (kStage) {
             const V *xin = in + b0 * ld;
             const int per = M + 1;
-            for (int idx = threadIdx.x; idx < valid * per; idx += blockDim.x) {
-                const int l = idx / per;
-                cp_async_zfill<(int)sizeof(V)>(xs + idx, xin + (long long)l * ld + (idx - l * per), true);
+            if (ld == per) {
+                // one contiguous run: one bulk copy
+                if (!stage_contiguous(xs, xin, valid * per)) {
+                    if (threadIdx.x == 0 && d.err) atomicExch(d.err, 1u);
+                    return;
+                }
+            } else {
+                for (int idx = threadIdx.x; idx < valid * per; idx += blockDim.x) {
+                    const int l = idx / per;
+                    cp_async_zfill<(int)sizeof(V)>(xs + idx, xin + (long long)l * ld + (idx - l * per), true);
+                }
+                cp_async_commit();
+                cp_async_wait<0>();
+                __syncthreads();
             }
-            cp_async_commit();
-            cp_async_wait<0>();
-            __syncthreads();
         }
         const V *xsrc = kStage ? xs : in + b0 * ld;
         const int xld = kStage ? M + 1 : ld;
