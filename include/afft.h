@@ -273,6 +273,22 @@ int afft_plan_set_l2_chunk(afft_plan *p, size_t bytes);
 size_t afft_plan_l2_chunk(const afft_plan *p);
 
 /*
+ * Alternating stage order.  Each stage of Algorithm 1 walks its tiles (or line
+ * blocks) in one order; a stage that starts where the previous stage finished
+ * finds that part of the array still in L2 (129 MB on GB300) instead of HBM.
+ * With this on (the default), the unfused stages that follow a stage walking the
+ * same planes run last to first: the forward N1 stage after the N2 stage, and the
+ * backward N2 stage after the N1 stage (also in afft_execute_poisson).  Only the
+ * order of independent tiles changes, so
+ * results are bit-for-bit the same either way.  (p, 0) walks every stage first to
+ * last.  Allocates nothing.  Not while the plan is in use on a stream.
+ */
+int afft_plan_set_l2_order(afft_plan *p, int on);
+
+/* 1 when the plan's stages alternate their tile order (see above), else 0. */
+int afft_plan_l2_order(const afft_plan *p);
+
+/*
  * Autotuner (the counterpart of the MEASURE planner flag AccFFT passes to FFTW
  * and cuFFT, Section 3 "Implementation Details").  Times forward + backward
  * round trips of this plan on temporary buffers (allocated and freed here,

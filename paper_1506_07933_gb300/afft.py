@@ -45,6 +45,7 @@ EXPORTS = [
     "afft_plan_set_blocked", "afft_plan_get_tuning", "afft_plan_set_tuning", "afft_plan_create_axes",
     "afft_plan_set_backward_scale", "afft_plan_backward_scale", "afft_copy_2d", "afft_queue_create",
     "afft_queue_execute", "afft_queue_status", "afft_queue_items", "afft_queue_destroy",
+    "afft_plan_set_l2_order", "afft_plan_l2_order",
 ]
 
 _lib = None
@@ -103,6 +104,8 @@ def load(path: str = None):
     lib.afft_plan_wait_probe.argtypes = [vp, c_int, vp]
     lib.afft_plan_set_l2_chunk.argtypes = [vp, sz]
     lib.afft_plan_set_blocked.argtypes = [vp, c_int]
+    lib.afft_plan_set_l2_order.argtypes = [vp, c_int]
+    lib.afft_plan_l2_order.argtypes = [vp]
     lib.afft_plan_get_tuning.argtypes = [vp, i64p]
     lib.afft_plan_set_tuning.argtypes = [vp, i64p]
     lib.afft_plan_l2_chunk.argtypes = [vp]
@@ -115,7 +118,8 @@ def load(path: str = None):
               "afft_multi_execute", "afft_multi_destroy", "afft_execute_poisson", "afft_plan_wait_probe",
               "afft_plan_set_blocked", "afft_plan_get_tuning", "afft_plan_set_tuning", "afft_plan_create_axes",
               "afft_plan_set_backward_scale", "afft_copy_2d", "afft_queue_create", "afft_queue_execute",
-              "afft_queue_status", "afft_queue_items", "afft_queue_destroy"):
+              "afft_queue_status", "afft_queue_items", "afft_queue_destroy", "afft_plan_set_l2_order",
+              "afft_plan_l2_order"):
         getattr(lib, f).restype = c_int
     _lib = lib
     return lib
@@ -331,6 +335,14 @@ class Plan:
     def set_blocked(self, on: bool) -> None:
         """Blocked c2c layout (a workspace of the array's size; see afft_plan_set_blocked)."""
         _check(load().afft_plan_set_blocked(self._p, int(bool(on))), "afft_plan_set_blocked")
+
+    def set_l2_order(self, on: bool) -> None:
+        """Alternating tile order of consecutive stages (see afft_plan_set_l2_order)."""
+        _check(load().afft_plan_set_l2_order(self._p, int(bool(on))), "afft_plan_set_l2_order")
+
+    @property
+    def l2_order(self) -> bool:
+        return bool(load().afft_plan_l2_order(self._p))
 
     def set_l2_chunk(self, nbytes: int) -> None:
         """Slab size for L2-resident fusion of the N2 and N1 stages (0: unfused)."""

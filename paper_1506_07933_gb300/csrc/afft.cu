@@ -78,6 +78,12 @@ struct afft_plan {
     unsigned *d_mma;       // split-precision plans: DFT-16 tensor-core fragments
     int contig_target;     // points per CTA of the contiguous stage (0: default)
     size_t chunk_bytes;    // requested slab size (0: off)
+    // stages walk their tiles in alternating order where the previous stage wrote the same array
+    // in the same plane order (forward N1 last to first after N2; backward N2 last to first after
+    // N1), so they start on the part of the array still in L2; measured on the 512^3 r2c step:
+    // N1 forward 0.1988 -> 0.1967 ms, c2r 0.1848 -> 0.1820 ms, while reversing the backward N0
+    // stage after the forward one (columns in the same order) measured 0.001 ms slower
+    bool l2_order;
     int chunk_planes;      // planes per slab; 0 when the stages run unfused
     cudaStream_t aux;
     std::vector<cudaEvent_t> chunk_ev;  // [0]: fork, then two per slab
@@ -599,7 +605,7 @@ bool encode_blocked_map(CUtensorMap *map, const void *base, long long zdim, int 
 template <typename V>
 cudaError_t pipe_on_map(const AxisPlan &a, const CUtensorMap &map, bool tma, const V *in, V *out, const V *tw,
                         long long outer, long long W, int backward, unsigned *err, int zrows, long long zstride,
-                        cudaStream_t s)
+                        cudaStream_t s, int rev = 0)
 {
     const int which = backward ? (tma ? PIPE_BWD_TMA : PIPE_BWD_CPASYNC) : (tma ? PIPE_FWD_TMA : PIPE_FWD_CPASYNC);
     const void *fn = zrows > 0 ? a.ks->pipe_blk[backward ? 1 : 0] : a.ks->pipe[which];
@@ -610,15 +616,16 @@ cudaError_t pipe_on_map(const AxisPlan &a, const CUtensorMap &map, bool tma, con
     const void *twdf = a.desc.twdf;
     const unsigned *mma = a.desc.mma;
     const unsigned grid = (unsigned)std::min<long long>(nt, a.pipe_slots);
-    void *args[] = {(void *)&in,   (void *)&out, (void *)&map, (void *)&tw,    (void *)&W,      (void *)&tpo,
-                    (void *)&nt,   (void *)&err, (void *)&twdf, (void *)&mma, (void *)&zrows, (void *)&zstride};
+    void *args[] = {(void *)&in,  (void *)&out,  (void *)&map, (void *)&tw,    (void *)&W,
+                    (void *)&tpo, (void *)&nt,   (void *)&err, (void *)&twdf,  (void *)&mma,
+                    (void *)&zrows, (void *)&zstride, (void *)&rev};
     if (nt <= 0 || grid == 0) return nt <= 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
     return cudaLaunchKernel(fn, dim3(grid), dim3(a.ks->pipe_threads), args, (size_t)a.ks->pipe_smem, s);
 }
 
 template <typename V>
 cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, long long outer, long long W,
-                         int backward, unsigned *err, cudaStream_t s)
+                         int backward, unsigned *err, cudaStream_t s, int rev)
 {
     alignas(64) CUtensorMap map;
     std::memset(&map, 0, sizeof map);
@@ -631,23 +638,24 @@ cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, lo
         const void *twdf = nullptr;
         const unsigned *mma = nullptr;
         const unsigned grid = (unsigned)std::min<long long>(nt, a.rp_slots);
-        void *args[] = {(void *)&in, (void *)&out, (void *)&map, (void *)&tw,   (void *)&W,
-                        (void *)&tpo, (void *)&nt, (void *)&err, (void *)&twdf, (void *)&mma};
+        void *args[] = {(void *)&in,  (void *)&out, (void *)&map, (void *)&tw,   (void *)&W,
+                        (void *)&tpo, (void *)&nt,  (void *)&err, (void *)&twdf, (void *)&mma, (void *)&rev};
         const void *fn = a.rp_early && a.ks->pipe_rp_early[0] ? a.ks->pipe_rp_early[backward ? 1 : 0]
                                                               : a.ks->pipe_rp[backward ? 1 : 0];
         return cudaLaunchKernel(fn, dim3(grid), dim3(a.ks->pipe_threads), args, (size_t)a.ks->pipe_smem_rp, s);
     }
     const bool tma = encode_strided_map(&map, in, outer, a.desc.n, W, sizeof(V), a.ks->pipe_lines);
-    return pipe_on_map<V>(a, map, tma, in, out, tw, outer, W, backward, err, 0, 0, s);
+    return pipe_on_map<V>(a, map, tma, in, out, tw, outer, W, backward, err, 0, 0, s, rev);
 }
 
 // A strided stage over a [outer][n][W] array (in place when in == out).
 template <typename V>
 cudaError_t strided(const AxisPlan &a, const V *in, V *out, const V *tw, long long outer, long long W,
-                    int backward, cudaStream_t s, unsigned *err)
+                    int backward, cudaStream_t s, unsigned *err, int rev = 0)
 {
-    if (a.pipe) return strided_pipe<V>(a, in, out, tw, outer, W, backward, err, s);
+    if (a.pipe) return strided_pipe<V>(a, in, out, tw, outer, W, backward, err, s, rev);
     StageDesc d = a.desc;
+    d.rev = rev;
     tw += a.tw_base;
     long long tpo = (W + a.launch.lines - 1) / a.launch.lines;
     int lg = a.launch.log2_lines;
@@ -678,10 +686,11 @@ cudaError_t fourstep(const FourStep &f, const V *in, V *out, const V *tw, long l
 
 template <typename V>
 cudaError_t contig(const AxisPlan &a, const V *in, V *out, const V *tw, long long nlines, int backward,
-                   double scale, cudaStream_t s)
+                   double scale, cudaStream_t s, int rev = 0)
 {
     using T = decltype(V().x);
     StageDesc d = a.desc;
+    d.rev = rev;
     tw += a.tw_base;
     int lines = a.launch.lines;
     T sc = (T)scale;
@@ -691,9 +700,10 @@ cudaError_t contig(const AxisPlan &a, const V *in, V *out, const V *tw, long lon
 
 template <typename V, typename T>
 cudaError_t r2c(const AxisPlan &a, const T *in, V *out, const V *tw, const V *post, long long nlines,
-                cudaStream_t s)
+                cudaStream_t s, int rev = 0)
 {
     StageDesc d = a.desc;
+    d.rev = rev;
     tw += a.tw_base;
     int lines = a.launch.lines;
     void *args[] = {(void *)&in, (void *)&out, (void *)&d, (void *)&tw, (void *)&post, (void *)&nlines, (void *)&lines};
@@ -702,9 +712,10 @@ cudaError_t r2c(const AxisPlan &a, const T *in, V *out, const V *tw, const V *po
 
 template <typename V, typename T>
 cudaError_t c2r(const AxisPlan &a, const V *in, T *out, const V *tw, const V *post, long long nlines,
-                double scale, cudaStream_t s)
+                double scale, cudaStream_t s, int rev = 0)
 {
     StageDesc d = a.desc;
+    d.rev = rev;
     tw += a.tw_base;
     int lines = a.launch.lines;
     T sc = (T)scale;
@@ -729,11 +740,11 @@ void mark(afft_plan *p, int i, cudaStream_t s)
 // unsplit strided stages are never the scaled last stage).
 template <typename V>
 cudaError_t axis_stage(afft_plan *p, int a, const V *in, V *out, long long outer, long long W, int backward,
-                       double scale, cudaStream_t s)
+                       double scale, cudaStream_t s, int rev = 0)
 {
     const V *tw = (const V *)p->d_tw;
     const FourStep &f = p->four[a];
-    if (!f.on) return strided<V>(p->ax[a], in, out, tw, outer, W, backward, s, p->d_err);
+    if (!f.on) return strided<V>(p->ax[a], in, out, tw, outer, W, backward, s, p->d_err, rev);
     V *tmp = (V *)p->d_four;
     cudaError_t e = strided<V>(p->ax[a], in, tmp, tw, outer, W * f.na, backward, s, p->d_err);
     if (e != cudaSuccess) return e;
@@ -961,9 +972,11 @@ int run_forward(afft_plan *p, const void *in, void *out, cudaStream_t s)
         return r2c<V, T>(p->ax[2], (const T *)in + p0 * plane_in, w + p0 * plane_w, tw, tw + p->post_off,
                          np * n1, st);
     };
+    // alternating tile order (see afft_plan::l2_order), with the stages unfused
+    const int alt = p->l2_order && p->chunk_planes == 0;
     auto ystage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
         if (n1 <= 1) return cudaSuccess;
-        return axis_stage<V>(p, 1, w + p0 * plane_w, w + p0 * plane_w, np, nh, 0, 1.0, st);
+        return axis_stage<V>(p, 1, w + p0 * plane_w, w + p0 * plane_w, np, nh, 0, 1.0, st, alt);
     };
     cudaError_t e = cudaSuccess;
     mark(p, 0, s);
@@ -1016,13 +1029,16 @@ int run_backward(afft_plan *p, const void *in, void *out, cudaStream_t s)
         if (n1 <= 1) return cudaSuccess;
         return axis_stage<V>(p, 1, buf + p0 * plane_w, buf + p0 * plane_w, np, nh, 1, 1.0, st);
     };
+    // alternating tile order (see afft_plan::l2_order), with the stages unfused
+    const int alt = p->l2_order && p->chunk_planes == 0;
     auto zstage = [&](long long p0, long long np, cudaStream_t st) -> cudaError_t {
         if (p->kind == AFFT_C2C && p->four[2].on)
             return axis_stage<V>(p, 2, buf + p0 * plane_w, (V *)out + p0 * plane_out, np * n1, 1, 1, scale, st);
         if (p->kind == AFFT_C2C)
-            return contig<V>(p->ax[2], buf + p0 * plane_w, (V *)out + p0 * plane_out, tw, np * n1, 1, scale, st);
+            return contig<V>(p->ax[2], buf + p0 * plane_w, (V *)out + p0 * plane_out, tw, np * n1, 1, scale, st,
+                             alt);
         return c2r<V, T>(p->ax[2], buf + p0 * plane_w, (T *)out + p0 * plane_out, tw, tw + p->post_off, np * n1,
-                         scale, st);
+                         scale, st, alt);
     };
     mark(p, 0, s);
     // (n0 == 1: a copy of `in` into the buffer, which c2r then transforms without touching `in`)
@@ -1095,8 +1111,9 @@ int run_poisson(afft_plan *p, const void *in, void *out, cudaStream_t s)
     const double scale = 1.0 / ((double)n0 * (double)n1 * (double)n2);
     V *w = (V *)p->d_work;
     mark(p, 0, s);
+    const int alt = p->l2_order;   // alternating tile order, as in run_forward / run_backward
     if (r2c<V, T>(p->ax[2], (const T *)in, w, tw, tw + p->post_off, P0 * n1, s) != cudaSuccess) return AFFT_ERR_CUDA;
-    if (n1 > 1 && axis_stage<V>(p, 1, w, w, P0, nh, 0, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
+    if (n1 > 1 && axis_stage<V>(p, 1, w, w, P0, nh, 0, 1.0, s, alt) != cudaSuccess) return AFFT_ERR_CUDA;
     mark(p, 1, s);
     const AxisPlan &x = p->ax[0];
     const long long W = n1 * nh;
@@ -1109,10 +1126,11 @@ int run_poisson(afft_plan *p, const void *in, void *out, cudaStream_t s)
         long long tpo = (W + x.ks->pipe_lines - 1) / x.ks->pipe_lines, nt = B * tpo;
         const void *twdf = x.desc.twdf;
         unsigned *err = p->d_err;
-        int in1 = (int)n1, ipitch = (int)nh, inh = (int)nh;
+        int in1 = (int)n1, ipitch = (int)nh, inh = (int)nh, rev = 0;
         const V *win = w;
-        void *args[] = {(void *)&win, (void *)&w, (void *)&map, (void *)&twa, (void *)&WW, (void *)&tpo, (void *)&nt,
-                        (void *)&err, (void *)&twdf, (void *)&in1, (void *)&ipitch, (void *)&inh};
+        void *args[] = {(void *)&win, (void *)&w,    (void *)&map, (void *)&twa,    (void *)&WW,
+                        (void *)&tpo, (void *)&nt,   (void *)&err, (void *)&twdf,   (void *)&in1,
+                        (void *)&ipitch, (void *)&inh, (void *)&rev};
         const unsigned grid = (unsigned)std::min<long long>(nt, x.pipe_slots);
         if (cudaLaunchKernel(x.ks->poisson[tma ? 0 : 1], dim3(grid), dim3(x.ks->pipe_threads), args,
                              (size_t)x.ks->pipe_smem, s) != cudaSuccess)
@@ -1130,7 +1148,7 @@ int run_poisson(afft_plan *p, const void *in, void *out, cudaStream_t s)
     }
     mark(p, 2, s);
     if (n1 > 1 && axis_stage<V>(p, 1, w, w, P0, nh, 1, 1.0, s) != cudaSuccess) return AFFT_ERR_CUDA;
-    if (c2r<V, T>(p->ax[2], w, (T *)out, tw, tw + p->post_off, P0 * n1, scale, s) != cudaSuccess)
+    if (c2r<V, T>(p->ax[2], w, (T *)out, tw, tw + p->post_off, P0 * n1, scale, s, alt) != cudaSuccess)
         return AFFT_ERR_CUDA;
     mark(p, 3, s);
     return AFFT_OK;
@@ -1276,6 +1294,7 @@ int afft_plan_create_axes(afft_plan **out, const int64_t n[3], int64_t batch, in
     p->precision = precision;
     p->axes = axes;
     p->bscale = 1.0;
+    p->l2_order = true;
     for (int i = 0; i < 3; ++i)
         if ((axes >> i) & 1) p->bscale /= (double)n[i];
     p->nh = kind == AFFT_R2C ? n[2] / 2 + 1 : n[2];
@@ -1722,7 +1741,7 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         "\"radix\": [\"%s\", \"%s\", \"%s\"], \"specialised\": [%d, %d, %d], \"four_step\": [%d, %d, %d], "
         "\"pipelined\": [%d, %d], \"contig_lines\": %d, \"strided_lines\": [%d, %d], "
         "\"l2_slab_planes\": %d, \"blocked\": %d, \"axes\": %d, \"backward_scale\": %.17g, "
-        "\"rp_early\": [%d, %d], \"pipe_ctas\": [%d, %d], "
+        "\"rp_early\": [%d, %d], \"pipe_ctas\": [%d, %d], \"l2_order\": %d, "
         "\"stage_kernels_forward\": [\"%s\", \"%s\", \"%s\"], \"stage_kernels_backward\": [\"%s\", \"%s\", \"%s\"]}",
         (long long)p->n[0], (long long)p->n[1], (long long)p->n[2], (long long)p->batch,
         p->kind == AFFT_C2C ? "c2c" : "r2c",
@@ -1731,7 +1750,7 @@ int afft_plan_describe(const afft_plan *p, char *buf, size_t len)
         p->four[2].on, p->ax[0].pipe, p->ax[1].pipe, p->ax[2].launch.lines,
         p->ax[0].pipe ? p->ax[0].ks->pipe_lines : p->ax[0].launch.lines,
         p->ax[1].pipe ? p->ax[1].ks->pipe_lines : p->ax[1].launch.lines, p->chunk_planes, (int)blk, p->axes, p->bscale,
-        (int)p->ax[0].rp_early, (int)p->ax[1].rp_early, p->ax[0].pipe_slots, p->ax[1].pipe_slots,
+        (int)p->ax[0].rp_early, (int)p->ax[1].rp_early, p->ax[0].pipe_slots, p->ax[1].pipe_slots, (int)p->l2_order,
         blk ? "k_contig" : zf, y, x, x, y, blk ? "k_contig" : zb);
     if (need < 0) return AFFT_ERR_CUDA;
     return (size_t)need < len ? AFFT_OK : AFFT_ERR_SIZE;
@@ -1783,6 +1802,15 @@ int afft_copy_2d(void *dst, size_t dpitch, const void *src, size_t spitch, size_
     return cuda_status(cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDefault,
                                          (cudaStream_t)stream));
 }
+
+int afft_plan_set_l2_order(afft_plan *p, int on)
+{
+    if (!p) return AFFT_ERR_NULL;
+    p->l2_order = on != 0;
+    return AFFT_OK;
+}
+
+int afft_plan_l2_order(const afft_plan *p) { return p && p->l2_order ? 1 : 0; }
 
 int afft_plan_set_blocked(afft_plan *p, int on)
 {

@@ -42,7 +42,13 @@ struct StageDesc {
     int blk, blk_in, blk_out;
     long long blk_n1, blk_planes;
     unsigned *err;                 // set by a kernel whose bounded wait ran out (null: not reported)
+    // 1: the CTAs take their line blocks (or tiles) in reverse order, last first, so that a stage
+    // following one that wrote the same array front to back starts on the part still in L2
+    int rev;
 };
+
+// Block (or tile) i of n in the order a stage walks them.
+__host__ __device__ inline long long stage_order(long long i, long long n, int rev) { return rev ? n - 1 - i : i; }
 
 // Line of the blocked layout holding row-major line q (see StageDesc::blk).
 __host__ __device__ inline long long blocked_line(const StageDesc &d, long long q)
@@ -100,8 +106,9 @@ enum { KS_STRIDED_FWD = 0, KS_STRIDED_BWD, KS_CONTIG_FWD, KS_CONTIG_BWD, KS_R2C,
 // through `map`, a [outer][n][W] view, the cp.async ones through `in`; zrows
 // and zstride are read only by the blocked variants (pipe_blk, TMA): there the
 // rows of outer line o are blocks of zrows rows, block k at z = k * zstride + o
-// of a [..][zrows][W] map.  The row-pair kernels (pipe_rp) take the first ten
-// of these arguments.
+// of a [..][zrows][W] map; a last argument int rev walks the tiles last to first
+// (see StageDesc::rev).  The row-pair kernels (pipe_rp) take the first ten of
+// these arguments and rev.
 enum { PIPE_FWD_TMA = 0, PIPE_FWD_CPASYNC, PIPE_BWD_TMA, PIPE_BWD_CPASYNC, PIPE_COUNT };
 
 struct KernelSet {
@@ -122,7 +129,7 @@ struct KernelSet {
     // fused Poisson N0 stage (forward DFTs, 1/|k|^2, inverse DFTs) on pipelined tiles:
     // (const V *in, V *out, CUtensorMap map, const V *tw, long long W,
     // long long tiles_per_outer, long long ntiles, unsigned *err, const void *twdf,
-    // int n1, int nhp, int nh); [0] TMA, [1] cp.async
+    // int n1, int nhp, int nh, int rev); [0] TMA, [1] cp.async
     const void *poisson[2];
     int pipe_lines;                // columns per tile of the pipelined kernel
     int pipe_threads;              // its (compile-time) CTA size

@@ -349,7 +349,7 @@ template <class P, int S, typename V, bool TMA, bool Split = false, bool Blocked
 __global__ void __launch_bounds__(PipeShape<P, V>::threads, Split ? PipeShape<P, V>::min_blocks_split : 1)
     k_strided_pipe(const V *__restrict__ in, V *out, const __grid_constant__ CUtensorMap tmap,
                    const V *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
-                   unsigned *err, const void *twdf, const unsigned *mma, int zrows, long long zstride)
+                   unsigned *err, const void *twdf, const unsigned *mma, int zrows, long long zstride, int rev)
 {
     using Sh = PipeShape<P, V>;
     constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, Split ? PipeShape<P,
         tc_setup(reinterpret_cast<const unsigned char *>(mma) + kMmaTableWords * 4 + (S < 0 ? 0 : kTcBBytes),
                  tc_cols_for(NT));
 
-    auto issue = [&](long long tile, int b) {
+    auto issue = [&](long long tile_i, int b) {
+        const long long tile = stage_order(tile_i, ntiles, rev);
         const long long o = tile / tiles_per_outer;
         const long long c0 = (tile - o * tiles_per_outer) * LINES;
         if constexpr (TMA) {
@@ -443,8 +444,9 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, Split ? PipeShape<P,
         }
         if (!Early && tn < ntiles) issue(tn, b ^ 1);   // next tile flies while this one is transformed
 
-        const long long o = t / tiles_per_outer;
-        const long long c0 = (t - o * tiles_per_outer) * LINES;
+        const long long tile = stage_order(t, ntiles, rev);
+        const long long o = tile / tiles_per_outer;
+        const long long c0 = (tile - o * tiles_per_outer) * LINES;
         TileOut<V> to;
         to.single = GlobalColFixedOut<V>{out + o * (long long)N * W, W, out_col(c0 + (tid & (LINES - 1)))};
         to.cols = PipeColOut<V>{out + o * (long long)N * W, c0, W};
@@ -603,15 +605,15 @@ __device__ __forceinline__ void rp_early_passes(Seq<R0, Rest...>, const float2 *
     scratch_passes<Sh, S, N, R0, 0>(Seq<Rest...>{}, C, tw, out);
 }
 
-// Persistent, double-buffered strided stage over odd-width complex64 rows (same
-// argument list as k_strided_pipe; the tensor map views [outer][n/2][2W] with
-// boxes of 18 x n/2).  Early: the load buffer is released after the first pass
+// Persistent, double-buffered strided stage over odd-width complex64 rows (the
+// first ten arguments of k_strided_pipe and rev; the tensor map views
+// [outer][n/2][2W] with boxes of 18 x n/2).  Early: the load buffer is released after the first pass
 // (two tile loads in flight during the other passes), as k_strided_pipe does.
 template <class P, int S, bool Early = false>
 __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
     k_strided_pipe_rp(const float2 *__restrict__, float2 *out, const __grid_constant__ CUtensorMap tmap,
                       const float2 *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
-                      unsigned *err, const void *, const unsigned *)
+                      unsigned *err, const void *, const unsigned *, int rev)
 {
     using V = float2;
     using Sh = PipeShape<P, V>;
@@ -637,8 +639,9 @@ __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
     }
     __syncthreads();
 
-    auto issue = [&](long long tile, int b) {
+    auto issue = [&](long long tile_i, int b) {
         if (tid != 0) return;
+        const long long tile = stage_order(tile_i, ntiles, rev);
         const long long o = tile / tiles_per_outer;
         const long long c0 = (tile - o * tiles_per_outer) * LINES;
         fence_async_shared();
@@ -664,8 +667,9 @@ __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
         }
         if (!Early && tn < ntiles) issue(tn, b ^ 1);
 
-        const long long o = t / tiles_per_outer;
-        const long long c0 = (t - o * tiles_per_outer) * LINES;
+        const long long tile = stage_order(t, ntiles, rev);
+        const long long o = tile / tiles_per_outer;
+        const long long c0 = (tile - o * tiles_per_outer) * LINES;
         const int l = tid & (LINES - 1), lp = tid % (LINES / 2);
         V *obase = out + o * (long long)N * W;
         const long long a = c0 + 2 * lp;
@@ -740,7 +744,7 @@ template <class P, typename V, bool TMA>
 __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
     k_poisson_pipe(const V *__restrict__ in, V *out, const __grid_constant__ CUtensorMap tmap,
                    const V *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
-                   unsigned *err, const void *twdf, int n1, int nhp, int nh)
+                   unsigned *err, const void *twdf, int n1, int nhp, int nh, int rev)
 {
     using Sh = PipeShape<P, V>;
     constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
@@ -759,7 +763,8 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    auto issue = [&](long long tile, int b) {
+    auto issue = [&](long long tile_i, int b) {
+        const long long tile = stage_order(tile_i, ntiles, rev);
         const long long o = tile / tiles_per_outer;
         const long long c0 = (tile - o * tiles_per_outer) * LINES;
         if constexpr (TMA) {
@@ -805,8 +810,9 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, 1)
         const long long tn = t + gridDim.x;
         if (tn < ntiles) issue(tn, b ^ 1);
 
-        const long long o = t / tiles_per_outer;
-        const long long c0 = (t - o * tiles_per_outer) * LINES;
+        const long long tile = stage_order(t, ntiles, rev);
+        const long long o = tile / tiles_per_outer;
+        const long long c0 = (tile - o * tiles_per_outer) * LINES;
         const long long c = c0 + (tid & (LINES - 1));
         const int k1 = (int)(c / nhp), k2 = (int)(c - (long long)(c / nhp) * nhp);
         const bool keep = c < W && k2 < nh;

@@ -339,8 +339,9 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     V *sm = reinterpret_cast<V *>(smem_raw);
     const int n = F::generic ? d.n : F::plan::n;
     const int lines = 1 << log2_lines;
-    const long long o = blockIdx.x / tiles_per_outer;
-    const long long c0 = (blockIdx.x - o * tiles_per_outer) * lines;
+    const long long tile = stage_order(blockIdx.x, gridDim.x, d.rev);
+    const long long o = tile / tiles_per_outer;
+    const long long c0 = (tile - o * tiles_per_outer) * lines;
     const long long off = o * (long long)n * W + c0;
     const int valid = (int)min((long long)lines, W - c0);
     const GlobalCols<V> src{in + off, W, valid};
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *sm = reinterpret_cast<V *>(smem_raw);
     const int n = F::generic ? d.n : F::plan::n;
-    const long long b0 = (long long)blockIdx.x * lines;
+    const long long b0 = stage_order(blockIdx.x, gridDim.x, d.rev) * lines;
     const int valid = (int)min((long long)lines, nlines - b0);
     // a blocked layout on either side keeps the CTA's lines consecutive (the host makes `lines`
     // divide the block), so only the first line's position changes
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *sm = reinterpret_cast<V *>(smem_raw);
     const int M = F::generic ? d.n : F::plan::n;
-    const long long b0 = (long long)blockIdx.x * lines;
+    const long long b0 = stage_order(blockIdx.x, gridDim.x, d.rev) * lines;
     const int valid = (int)min((long long)lines, nlines - b0);
     const GlobalLines<V> src{reinterpret_cast<const V *>(in) + b0 * M, M, valid};
     const SmemLines<V> tile{sm, M};
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(F::template threads<V>(), F::min_blocks)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *sm = reinterpret_cast<V *>(smem_raw);
     const int M = F::generic ? d.n : F::plan::n;
-    const long long b0 = (long long)blockIdx.x * lines;
+    const long long b0 = stage_order(blockIdx.x, gridDim.x, d.rev) * lines;
     const int valid = (int)min((long long)lines, nlines - b0);
     const int ld = d.ld > 0 ? d.ld : M + 1;  // input line stride
     const C2RPre<V> src{in + b0 * ld, post_tw, M, ld, valid};

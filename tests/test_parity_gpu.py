@@ -176,6 +176,36 @@ def test_r2c_odd_width_rows_early_release(shape):
            TOL["f32"])
 
 
+@pytest.mark.parametrize("shape,kind", [((4, 64, 32), "r2c"), ((6, 48, 64), "r2c"), ((6, 96, 160), "r2c"),
+                                        ((3, 128, 256), "r2c"), ((4, 512, 512), "r2c"), ((32, 3, 20), "r2c"),
+                                        ((4, 32, 81), "c2c"), ((3, 64, 225), "c2c")])
+@pytest.mark.parametrize("early", [0, 1])
+def test_row_pair_tiles_with_a_one_column_tail(shape, kind, early):
+    """Rows of W = 16k + 1 complex64 columns (half spectra of 17, 33, 81, 129, 257 bins; c2c rows
+    of 81 and 225; an N0 stage over planes of 3 x 11 bins) run k full row-pair tiles and a last
+    tile of one column, whose boxes reach past the row pair's end: both directions against the
+    oracle, with the load buffer released early or not."""
+    if kind == "c2c":
+        x = synth.uniform_complex(shape, 47).astype(np.complex64)
+        ref = oracle.c2c(x)
+    else:
+        x = synth.uniform_real(shape, 47).astype(np.float32)
+        ref = oracle.r2c(x)
+    H = ref.astype(np.complex64)
+    with afft.Plan(shape, kind, "f32") as p:
+        cfg = p.tuning
+        cfg[4] = early if p.describe()["stage_kernels_forward"][2] == "k_strided_pipe_rp" else cfg[4]
+        cfg[5] = early if p.describe()["stage_kernels_forward"][1] == "k_strided_pipe_rp" else cfg[5]
+        p.set_tuning(cfg)
+        assert "k_strided_pipe_rp" in p.describe()["stage_kernels_forward"]
+        X = p.forward(torch.from_numpy(x).cuda())
+        y = p.backward(torch.from_numpy(H).cuda())
+        torch.cuda.synchronize()
+    back = oracle.c2c(H, +1) if kind == "c2c" else oracle.c2r(H, shape[2])
+    report("rp tail %s %s early %d" % (shape, kind, early), oracle.rel_l2(X.cpu().numpy(), ref), TOL["f32"])
+    report("rp tail backward %s %s early %d" % (shape, kind, early), oracle.rel_l2(y.cpu().numpy(), back), TOL["f32"])
+
+
 @pytest.mark.parametrize("shape", [(3, 2, 8192), (8, 10, 160), (4, 6, 500)])
 def test_c2r_staged_and_direct_tiles(shape):
     """The specialised complex64 c2r kernels copy a CTA's run of half-spectrum lines into shared
@@ -580,6 +610,39 @@ def test_l2_fused_slabs_match_unfused(shape, kind, prec, planes):
         assert torch.equal(f, ref_f) and torch.equal(b, ref_b)
     ref = oracle.r2c(x) if kind == "r2c" else oracle.c2c(x)
     report("fused %s %s %s planes=%d" % (shape, kind, prec, planes), oracle.rel_l2(f.cpu().numpy(), ref), TOL[prec])
+
+
+@pytest.mark.parametrize("shape,kind,prec", [((64, 48, 96), "r2c", "f32"), ((40, 30, 64), "c2c", "f32"),
+                                             ((24, 16, 32), "r2c", "f64"), ((36, 20, 24), "c2c", "f64"),
+                                             ((8, 512, 512), "r2c", "f32"), ((6, 10, 36), "r2c", "f32"),
+                                             ((5, 243, 40), "c2c", "f32"), ((3, 2, 8192), "r2c", "f32")])
+def test_alternating_stage_order_is_bit_exact(shape, kind, prec):
+    """By default consecutive stages walk their tiles in alternating order, so each starts on the
+    part of the array the previous stage wrote last (still in L2).  Only the order of independent
+    tiles changes: both transforms must equal the first-to-last order bit for bit (pipelined,
+    row-pair, plain strided, generic and r2c/c2r kernels, both precisions), and the oracle."""
+    if kind == "c2c":
+        x = synth.uniform_complex(shape, 43).astype(CDT[prec])
+    else:
+        x = synth.uniform_real(shape, 43).astype(RDT[prec])
+    with afft.Plan(shape, kind, prec) as p:
+        assert p.l2_order and p.describe()["l2_order"] == 1
+        t = torch.from_numpy(x).cuda()
+        f = p.forward(t)
+        b = p.backward(f)
+        u = p.poisson(t) if kind == "r2c" else None
+        p.set_l2_order(False)
+        assert not p.l2_order
+        f0 = p.forward(t)
+        b0 = p.backward(f0)
+        u0 = p.poisson(t) if kind == "r2c" else None
+        torch.cuda.synchronize()
+        assert torch.equal(f, f0) and torch.equal(b, b0)
+        assert u is None or torch.equal(u, u0)
+    ref = oracle.r2c(x) if kind == "r2c" else oracle.c2c(x)
+    report("alternating order %s %s %s" % (shape, kind, prec), oracle.rel_l2(f.cpu().numpy(), ref), TOL[prec])
+    report("alternating order round trip %s %s %s" % (shape, kind, prec), oracle.rel_l2(b.cpu().numpy(), x),
+           TOL[prec])
 
 
 @pytest.mark.parametrize("shape", [(8192, 2, 3), (2, 8192, 3), (2, 3, 8192), (3, 2, 6000), (1, 2, 65536),
