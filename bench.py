@@ -247,9 +247,9 @@ def gpu_config(step_bytes, world, input_mb):
 
 
 # ------------------------------------------------------------- replicas -----
-# With N > 1 ranks every rank transforms its own field (replicas: the transform does
-# not shard on one node without an all-to-all, and none is built), so the step time
-# is the slowest rank's and the value adds up over ranks.
+# With `--decomp replicas` every rank transforms its own field, so the step time is the
+# slowest rank's and the value adds up over ranks (the default at N > 1 is the slab
+# decomposition, one transform over all ranks: see run_slab).
 
 def max_over_ranks(value, world, dist, device):
     """The largest of every rank's `value` (world == 1: the value itself)."""
@@ -662,7 +662,7 @@ def batched_workload(afft, torch, steps=10, warmup=3, count=200, seed=200):
     return out
 
 
-def serving_workload(torch, count=400, rate=200.0, saturation=200, loaded=700.0):
+def serving_workload(torch, count=1200, rate=200.0, saturation=200, loaded=700.0):
     """Spectral Poisson requests (sizes uniform over 64..512 cubed, 30% FP64, Poisson arrivals at
     `rate` per second): the continuous-batching server against one request at a time, in real time,
     then both again at `loaded` requests per second (near the GPU's capacity) and with every request
