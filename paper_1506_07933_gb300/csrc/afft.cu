@@ -547,8 +547,6 @@ EncodeTiledFn encode_tiled()
     return fn;
 }
 
-// TMA view of a [outer][n][W] complex array as 8-byte elements: dims
-// (W * C/8, n, outer), box (lines * C/8, min(n, 256), 1).
 // TMA view of a [outer][n][W] complex64 array with W odd as row pairs: dims
 // (2W, n/2, outer) 8-byte elements, box (lines + 2, n/2, 1) (k_strided_pipe_rp).
 bool encode_rowpair_map(CUtensorMap *map, const void *base, long long outer, int n, long long W, int lines)
@@ -565,6 +563,8 @@ bool encode_rowpair_map(CUtensorMap *map, const void *base, long long outer, int
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// TMA view of a [outer][n][W] complex array as 8-byte elements: dims
+// (W * C/8, n, outer), box (lines * C/8, min(n, 256), 1).
 bool encode_strided_map(CUtensorMap *map, const void *base, long long outer, int n, long long W, size_t C,
                         int lines)
 {
@@ -581,27 +581,30 @@ bool encode_strided_map(CUtensorMap *map, const void *base, long long outer, int
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The N1-stage map of the blocked c2c layout: a [zdim][rows][W] array (W complex of C bytes)
-// read in boxes of `lines` columns x `rows` rows.
-bool encode_blocked_map(CUtensorMap *map, const void *base, long long zdim, int rows, long long W, size_t C,
-                        int lines)
+// The N1-stage map of the blocked c2c layout: a [n / rows][planes][rows][W] array (W complex of C
+// bytes) read in boxes of `lines` columns x all n rows of one plane (every block of it).
+bool encode_blocked_map(CUtensorMap *map, const void *base, long long planes, int rows, int n, long long W,
+                        size_t C, int lines)
 {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
     const size_t per = C / 8;
-    if ((W * C) % 16 != 0 || ((uintptr_t)base) % 16 != 0 || W < lines || rows < 1 || rows > 256) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)(W * per), (cuuint64_t)rows, (cuuint64_t)zdim};
-    cuuint64_t strides[2] = {(cuuint64_t)(W * C), (cuuint64_t)(rows * W * C)};
-    cuuint32_t box[3] = {(cuuint32_t)(lines * per), (cuuint32_t)rows, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(base), dims, strides, box, estr,
+    if ((W * C) % 16 != 0 || ((uintptr_t)base) % 16 != 0 || W < lines || rows < 1 || rows > 256 || n % rows != 0 ||
+        n / rows > 256)
+        return false;
+    // [n / rows blocks][planes][rows][W]: one box of every block of a plane, rows in natural order
+    cuuint64_t dims[4] = {(cuuint64_t)(W * per), (cuuint64_t)rows, (cuuint64_t)planes, (cuuint64_t)(n / rows)};
+    cuuint64_t strides[3] = {(cuuint64_t)(W * C), (cuuint64_t)(rows * W * C), (cuuint64_t)(planes * rows * W * C)};
+    cuuint32_t box[4] = {(cuuint32_t)(lines * per), (cuuint32_t)rows, 1, (cuuint32_t)(n / rows)};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // The pipelined kernel over a [outer][n][W] stage whose tiles load through `map` (TMA) or
-// from `in` (cp.async); zrows > 0: the map holds each line's rows as blocks of zrows rows,
-// block k of outer line o at z = k zstride + o (the blocked c2c layout).
+// from `in` (cp.async); zrows > 0: the blocked c2c layout, the map a [n / zrows][outer][zrows][W]
+// view whose one 4-D box holds a tile's rows (encode_blocked_map).
 template <typename V>
 cudaError_t pipe_on_map(const AxisPlan &a, const CUtensorMap &map, bool tma, const V *in, V *out, const V *tw,
                         long long outer, long long W, int backward, unsigned *err, int zrows, long long zstride,
@@ -804,7 +807,7 @@ int set_blocked(afft_plan *p, bool on)
     const bool ok =
         encode_strided_map(&p->blk_map0, p->d_blk, (n1 / kBlk) * p->batch, (int)n0, kBlk * n2, C,
                            p->ax[0].ks->pipe_lines) &&
-        encode_blocked_map(&p->blk_map1, p->d_blk, (n1 / kBlk) * P0, kBlk, n2, C, p->ax[1].ks->pipe_lines);
+        encode_blocked_map(&p->blk_map1, p->d_blk, P0, kBlk, (int)n1, n2, C, p->ax[1].ks->pipe_lines);
     if (!ok) {
         cudaFree(p->d_blk);
         p->d_blk = nullptr;

@@ -103,10 +103,9 @@ enum { KS_STRIDED_FWD = 0, KS_STRIDED_BWD, KS_CONTIG_FWD, KS_CONTIG_BWD, KS_R2C,
 // const void *twdf, const unsigned *mma, int zrows, long long zstride) (twdf:
 // the float-float twiddles of an FP64 plan, or null; mma: the tensor-core
 // DFT-16 table of a split-precision plan, or null); the TMA variants read
-// through `map`, a [outer][n][W] view, the cp.async ones through `in`; zrows
-// and zstride are read only by the blocked variants (pipe_blk, TMA): there the
-// rows of outer line o are blocks of zrows rows, block k at z = k * zstride + o
-// of a [..][zrows][W] map; a last argument int rev walks the tiles last to first
+// through `map`, a [outer][n][W] view, the cp.async ones through `in`; the
+// blocked variants (pipe_blk, TMA) read a [n / zrows][outer][zrows][W] map, one
+// 4-D box per tile (zrows and zstride describe it for the host); a last argument int rev walks the tiles last to first
 // (see StageDesc::rev).  The row-pair kernels (pipe_rp) take the first ten of
 // these arguments and rev.
 enum { PIPE_FWD_TMA = 0, PIPE_FWD_CPASYNC, PIPE_BWD_TMA, PIPE_BWD_CPASYNC, PIPE_COUNT };

@@ -1,8 +1,9 @@
 """The blocked c2c layout's line mapping (blocked_line in csrc/afft_internal.h), compiled for the
 host with nvcc and checked on the CPU: it is a permutation of the lines; a CTA's run of lines
 (its count dividing the 32-line block) stays consecutive, so the contiguous stage remaps only its
-first line; the N0 stage's [(n1/32) batch][n0][32 n2] view and the N1 stage's boxes (block k of
-plane o at z = k batch n0 + o of a [..][32][n2] map) address exactly the lines the mapping gives."""
+first line; the N0 stage's [(n1/32) batch][n0][32 n2] view and the N1 stage's 4-D map
+[n1/32][batch n0][32][n2] (row r of block k of plane o at line (k batch n0 + o) 32 + r) address
+exactly the lines the mapping gives."""
 import os
 import shutil
 import subprocess
@@ -43,7 +44,7 @@ int main(int argc, char **argv)
             if ((o * n0 + i0) * W0 + (j %% blk) * n2 != blocked_line(d, pl * n1 + j) * n2) {
                 printf("N0 view at plane %%lld line %%lld\n", pl, j); return 1;
             }
-            const long long z = (j / blk) * P0 + pl;                     // N1 box: z, row j mod 32
+            const long long z = (j / blk) * P0 + pl;                     // N1 map: block j / 32, plane pl
             if (z * blk + j %% blk != blocked_line(d, pl * n1 + j)) { printf("N1 box at %%lld %%lld\n", pl, j); return 1; }
         }
     printf("ok\n");
