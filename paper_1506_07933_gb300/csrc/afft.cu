@@ -602,6 +602,25 @@ bool encode_blocked_map(CUtensorMap *map, const void *base, long long planes, in
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The same [outer][n][W] array for the blocked kernel variant: the n rows as n / R groups of R =
+// tma_box_rows(n), dims (W * C/8, R, outer, n / R), so that one 4-D box (all groups of line o)
+// holds a tile in natural row order.
+bool encode_grouped_map(CUtensorMap *map, const void *base, long long outer, int n, long long W, size_t C, int lines)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const size_t per = C / 8;
+    const int R = tma_box_rows(n);
+    if ((W * C) % 16 != 0 || ((uintptr_t)base) % 16 != 0 || W < lines || n / R > 256) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)(W * per), (cuuint64_t)R, (cuuint64_t)outer, (cuuint64_t)(n / R)};
+    cuuint64_t strides[3] = {(cuuint64_t)(W * C), (cuuint64_t)(n * W * C), (cuuint64_t)(R * W * C)};
+    cuuint32_t box[4] = {(cuuint32_t)(lines * per), (cuuint32_t)R, 1, (cuuint32_t)(n / R)};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // The pipelined kernel over a [outer][n][W] stage whose tiles load through `map` (TMA) or
 // from `in` (cp.async); zrows > 0: the blocked c2c layout, the map a [n / zrows][outer][zrows][W]
 // view whose one 4-D box holds a tile's rows (encode_blocked_map).
@@ -775,7 +794,8 @@ bool blocked_eligible(const afft_plan *p)
     for (int a = 0; a < 3; ++a)
         if (p->four[a].on) return false;
     const AxisPlan &x = p->ax[0], &y = p->ax[1], &z = p->ax[2];
-    if (x.pipe_slots <= 0 || y.pipe_slots <= 0 || !y.ks->pipe_blk[0] || p->n[1] % kBlk != 0) return false;
+    if (x.pipe_slots <= 0 || y.pipe_slots <= 0 || !x.ks->pipe_blk[0] || !y.ks->pipe_blk[0] || p->n[1] % kBlk != 0)
+        return false;
     if (z.launch.lines < 1 || kBlk % z.launch.lines != 0) return false;
     const size_t C = cplx_size(p->precision);
     return (p->n[2] * (long long)C) % 16 == 0 && p->n[2] >= y.ks->pipe_lines;
@@ -805,7 +825,7 @@ int set_blocked(afft_plan *p, bool on)
     std::memset(&p->blk_map0, 0, sizeof p->blk_map0);
     std::memset(&p->blk_map1, 0, sizeof p->blk_map1);
     const bool ok =
-        encode_strided_map(&p->blk_map0, p->d_blk, (n1 / kBlk) * p->batch, (int)n0, kBlk * n2, C,
+        encode_grouped_map(&p->blk_map0, p->d_blk, (n1 / kBlk) * p->batch, (int)n0, kBlk * n2, C,
                            p->ax[0].ks->pipe_lines) &&
         encode_blocked_map(&p->blk_map1, p->d_blk, P0, kBlk, (int)n1, n2, C, p->ax[1].ks->pipe_lines);
     if (!ok) {
@@ -837,7 +857,7 @@ int run_blocked(afft_plan *p, const void *in, void *out, int backward, cudaStrea
     if (contig<V>(z, (const V *)in, ws, tw, P0 * n1, backward, scale, s) != cudaSuccess) return AFFT_ERR_CUDA;
     mark(p, 1, s);
     if (pipe_on_map<V>(p->ax[0], p->blk_map0, true, ws, ws, tw, (n1 / kBlk) * p->batch, kBlk * n2, backward,
-                       p->d_err, 0, 0, s) != cudaSuccess)
+                       p->d_err, tma_box_rows((int)n0), 0, s) != cudaSuccess)
         return AFFT_ERR_CUDA;
     mark(p, 2, s);
     if (pipe_on_map<V>(p->ax[1], p->blk_map1, true, ws, (V *)out, tw, P0, n2, backward, p->d_err, kBlk, P0, s) !=
