@@ -622,25 +622,24 @@ bool encode_grouped_map(CUtensorMap *map, const void *base, long long outer, int
 }
 
 // The pipelined kernel over a [outer][n][W] stage whose tiles load through `map` (TMA) or
-// from `in` (cp.async); zrows > 0: the blocked c2c layout, the map a [n / zrows][outer][zrows][W]
-// view whose one 4-D box holds a tile's rows (encode_blocked_map).
+// from `in` (cp.async); grouped: the map is 4-D (encode_blocked_map, encode_grouped_map), one box
+// per tile, read by the kernel's blocked variant.
 template <typename V>
 cudaError_t pipe_on_map(const AxisPlan &a, const CUtensorMap &map, bool tma, const V *in, V *out, const V *tw,
-                        long long outer, long long W, int backward, unsigned *err, int zrows, long long zstride,
-                        cudaStream_t s, int rev = 0)
+                        long long outer, long long W, int backward, unsigned *err, bool grouped, cudaStream_t s,
+                        int rev = 0)
 {
     const int which = backward ? (tma ? PIPE_BWD_TMA : PIPE_BWD_CPASYNC) : (tma ? PIPE_FWD_TMA : PIPE_FWD_CPASYNC);
-    const void *fn = zrows > 0 ? a.ks->pipe_blk[backward ? 1 : 0] : a.ks->pipe[which];
-    if (zrows > 0 && (!tma || !fn)) return cudaErrorInvalidValue;
+    const void *fn = grouped ? a.ks->pipe_blk[backward ? 1 : 0] : a.ks->pipe[which];
+    if (grouped && (!tma || !fn)) return cudaErrorInvalidValue;
     tw += a.tw_base;
     long long tpo = (W + a.ks->pipe_lines - 1) / a.ks->pipe_lines;
     long long nt = outer * tpo;
     const void *twdf = a.desc.twdf;
     const unsigned *mma = a.desc.mma;
     const unsigned grid = (unsigned)std::min<long long>(nt, a.pipe_slots);
-    void *args[] = {(void *)&in,  (void *)&out,  (void *)&map, (void *)&tw,    (void *)&W,
-                    (void *)&tpo, (void *)&nt,   (void *)&err, (void *)&twdf,  (void *)&mma,
-                    (void *)&zrows, (void *)&zstride, (void *)&rev};
+    void *args[] = {(void *)&in,  (void *)&out, (void *)&map, (void *)&tw,   (void *)&W,
+                    (void *)&tpo, (void *)&nt,  (void *)&err, (void *)&twdf, (void *)&mma, (void *)&rev};
     if (nt <= 0 || grid == 0) return nt <= 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
     return cudaLaunchKernel(fn, dim3(grid), dim3(a.ks->pipe_threads), args, (size_t)a.ks->pipe_smem, s);
 }
@@ -667,7 +666,7 @@ cudaError_t strided_pipe(const AxisPlan &a, const V *in, V *out, const V *tw, lo
         return cudaLaunchKernel(fn, dim3(grid), dim3(a.ks->pipe_threads), args, (size_t)a.ks->pipe_smem_rp, s);
     }
     const bool tma = encode_strided_map(&map, in, outer, a.desc.n, W, sizeof(V), a.ks->pipe_lines);
-    return pipe_on_map<V>(a, map, tma, in, out, tw, outer, W, backward, err, 0, 0, s, rev);
+    return pipe_on_map<V>(a, map, tma, in, out, tw, outer, W, backward, err, false, s, rev);
 }
 
 // A strided stage over a [outer][n][W] array (in place when in == out).
@@ -857,10 +856,10 @@ int run_blocked(afft_plan *p, const void *in, void *out, int backward, cudaStrea
     if (contig<V>(z, (const V *)in, ws, tw, P0 * n1, backward, scale, s) != cudaSuccess) return AFFT_ERR_CUDA;
     mark(p, 1, s);
     if (pipe_on_map<V>(p->ax[0], p->blk_map0, true, ws, ws, tw, (n1 / kBlk) * p->batch, kBlk * n2, backward,
-                       p->d_err, tma_box_rows((int)n0), 0, s) != cudaSuccess)
+                       p->d_err, true, s) != cudaSuccess)
         return AFFT_ERR_CUDA;
     mark(p, 2, s);
-    if (pipe_on_map<V>(p->ax[1], p->blk_map1, true, ws, (V *)out, tw, P0, n2, backward, p->d_err, kBlk, P0, s) !=
+    if (pipe_on_map<V>(p->ax[1], p->blk_map1, true, ws, (V *)out, tw, P0, n2, backward, p->d_err, true, s) !=
         cudaSuccess)
         return AFFT_ERR_CUDA;
     mark(p, 3, s);

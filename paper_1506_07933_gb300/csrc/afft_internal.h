@@ -100,14 +100,14 @@ enum { KS_STRIDED_FWD = 0, KS_STRIDED_BWD, KS_CONTIG_FWD, KS_CONTIG_BWD, KS_R2C,
 // Pipelined strided kernels (persistent CTAs, double-buffered tiles), indexed
 // by PIPE_*.  Signature: (const V *in, V *out, CUtensorMap map, const V *tw,
 // long long W, long long tiles_per_outer, long long ntiles, unsigned *err,
-// const void *twdf, const unsigned *mma, int zrows, long long zstride) (twdf:
-// the float-float twiddles of an FP64 plan, or null; mma: the tensor-core
-// DFT-16 table of a split-precision plan, or null); the TMA variants read
-// through `map`, a [outer][n][W] view, the cp.async ones through `in`; the
-// blocked variants (pipe_blk, TMA) read a [n / zrows][outer][zrows][W] map, one
-// 4-D box per tile (zrows and zstride describe it for the host); a last argument int rev walks the tiles last to first
-// (see StageDesc::rev).  The row-pair kernels (pipe_rp) take the first ten of
-// these arguments and rev.
+// const void *twdf, const unsigned *mma, int rev) (twdf: the float-float
+// twiddles of an FP64 plan, or null; mma: the tensor-core DFT-16 table of a
+// split-precision plan, or null; rev: walk the tiles last to first, see
+// StageDesc::rev); the TMA variants read through `map`, a [outer][n][W] view,
+// the cp.async ones through `in`; the blocked variants (pipe_blk, TMA) read a
+// 4-D map [n / R][outer][R][W] with one box per tile (the blocked c2c
+// workspace, or the rows of a [outer][n][W] array grouped by R).  The row-pair
+// kernels (pipe_rp) take the same arguments.
 enum { PIPE_FWD_TMA = 0, PIPE_FWD_CPASYNC, PIPE_BWD_TMA, PIPE_BWD_CPASYNC, PIPE_COUNT };
 
 struct KernelSet {

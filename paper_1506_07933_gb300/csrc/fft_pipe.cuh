@@ -359,7 +359,7 @@ template <class P, int S, typename V, bool TMA, bool Split = false, bool Blocked
 __global__ void __launch_bounds__(PipeShape<P, V>::threads, Split ? PipeShape<P, V>::min_blocks_split : 1)
     k_strided_pipe(const V *__restrict__ in, V *out, const __grid_constant__ CUtensorMap tmap,
                    const V *__restrict__ tw, long long W, long long tiles_per_outer, long long ntiles,
-                   unsigned *err, const void *twdf, const unsigned *mma, int zrows, long long zstride, int rev)
+                   unsigned *err, const void *twdf, const unsigned *mma, int rev)
 {
     using Sh = PipeShape<P, V>;
     constexpr int N = P::n, LINES = Sh::lines, LG = Sh::lg, NT = Sh::threads, TILE = Sh::tile;
@@ -406,8 +406,8 @@ __global__ void __launch_bounds__(PipeShape<P, V>::threads, Split ? PipeShape<P,
                 constexpr int rows = Sh::box_rows;
                 constexpr int per = (int)sizeof(V) / 8;  // 8-byte elements per complex value
                 if constexpr (Blocked) {
-                    // blocked rows: the map is [N / zrows blocks][outer lines][zrows rows][W], so one
-                    // 4-D box (all blocks of line o) brings the tile's rows in natural order
+                    // a 4-D map [N / R groups][outer lines][R rows][W] (the blocked workspace, or rows
+                    // grouped by R): one box (all groups of line o) brings the tile in natural row order
                     tma_load_4d(buf0 + b * TILE, &tmap, (int)(c0 * per), 0, (int)o, 0, &bars[b]);
                 } else {
                     // boxes of at most 256 rows (measured on the 512^3 N0 stage: 0.175 ms with two
@@ -617,8 +617,8 @@ __device__ __forceinline__ void rp_early_passes(Seq<R0, Rest...>, const float2 *
 }
 
 // Persistent, double-buffered strided stage over odd-width complex64 rows (the
-// first ten arguments of k_strided_pipe and rev; the tensor map views
-// [outer][n/2][2W] with boxes of 18 x n/2).  Early: the load buffer is released after the first pass
+// arguments of k_strided_pipe; the tensor map views [outer][n/2][2W] with boxes
+// of 18 x n/2).  Early: the load buffer is released after the first pass
 // (two tile loads in flight during the other passes), as k_strided_pipe does.
 template <class P, int S, bool Early = false>
 __global__ void __launch_bounds__(PipeShape<P, float2>::threads, 1)
