@@ -3,7 +3,8 @@ host with nvcc and checked on the CPU: it is a permutation of the lines; a CTA's
 (its count dividing the 32-line block) stays consecutive, so the contiguous stage remaps only its
 first line; the N0 stage's [(n1/32) batch][n0][32 n2] view and the N1 stage's 4-D map
 [n1/32][batch n0][32][n2] (row r of block k of plane o at line (k batch n0 + o) 32 + r) address
-exactly the lines the mapping gives."""
+exactly the lines the mapping gives.  Also that stage_order (the alternating tile order of
+consecutive stages) visits every tile once, first to last or last to first."""
 import os
 import shutil
 import subprocess
@@ -46,6 +47,18 @@ int main(int argc, char **argv)
             }
             const long long z = (j / blk) * P0 + pl;                     // N1 map: block j / 32, plane pl
             if (z * blk + j %% blk != blocked_line(d, pl * n1 + j)) { printf("N1 box at %%lld %%lld\n", pl, j); return 1; }
+        }
+    // the alternating stage order walks every tile once: first to last, or last to first
+    for (long long n = 1; n <= 400; n += 37)
+        for (int rev = 0; rev < 2; ++rev) {
+            std::vector<char> seen(n, 0);
+            for (long long i = 0; i < n; ++i) {
+                const long long t = stage_order(i, n, rev);
+                if (t < 0 || t >= n || seen[t] || t != (rev ? n - 1 - i : i)) {
+                    printf("stage order %%lld of %%lld (rev %%d)\n", i, n, rev); return 1;
+                }
+                seen[t] = 1;
+            }
         }
     printf("ok\n");
     return 0;
